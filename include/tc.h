@@ -1,0 +1,128 @@
+/*
+ * tc.h -- C ABI of a single-GPU (GB300, sm_103a) library for the (T) triples
+ * correction of closed-shell, canonical-orbital CCSD(T).
+ *
+ * What is computed (Fajen, Kelly, Hohenstein, Martinez, "Accelerating CCSD(T)
+ * on GPUs", arXiv 2512.01055, Implementation Details, Eqs. 1-5):
+ *
+ *   E_(T) = sum_{a>=b>=c} (2 - d_ab - d_bc) sum_{ijk} (W + V)_ijk^abc
+ *           (4 W_ijk + W_jki + W_kij - 2 W_jik - 2 W_ikj - 2 W_kji)^abc / D_ijk^abc      (Eq. 1)
+ *   W_ijk^abc = P_ijk^abc [ sum_f G_if^ab t_kj^cf - sum_l G_ij^al t_lk^bc ]                  (Eqs. 2, 5)
+ *   V_ijk^abc = t_i^a G_jk^bc + t_j^b G_ik^ac + t_k^c G_ij^ab                                 (Eq. 3)
+ *   D_ijk^abc = e_i + e_j + e_k - e_a - e_b - e_c                                             (Fig. 4)
+ *
+ * with G_pq^rs = (pr|qs) (Mulliken) real two-electron integrals.  The library
+ * assumes the symmetries of real orbitals, (ia|bd) = (ia|db) and
+ * t_ij^ab = t_ji^ba; it does not check them.
+ *
+ * Array conventions (all row-major, C-contiguous, IEEE binary64):
+ *   eps  [o + v]         orbital energies, occupied first
+ *   t1   [o][v]          t_i^a
+ *   t2   [o][o][v][v]    t2[i][j][a][b] = t_ij^ab
+ *   ovvv [o][v][v][v]    ovvv[i][a][b][d] = (ia|bd)
+ *   ovoo [o][v][o][o]    ovoo[i][a][j][l] = (ia|jl)
+ *   ovov [o][v][o][v]    ovov[i][a][j][b] = (ia|jb)
+ * Indices: occupied i,j,k,l in [0,o); virtual a,b,c,d in [0,v).
+ *
+ * Ownership: the caller owns every array passed in.  Host arrays are copied
+ * before tc_energy / tc_submit return; device arrays passed to tc_energy_dev
+ * are read in place and must stay valid until that call returns.
+ *
+ * Errors: every entry point returns a tc_status; no exception, abort or
+ * longjmp crosses this boundary.  The text of the last failure of a context is
+ * available from tc_last_error.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_ctx tc_ctx;
+
+typedef enum {
+  TC_OK = 0,
+  TC_EINVAL = 1,       /* bad argument: o or v <= 0, NULL array, slices out of range ... */
+  TC_ENOMEM = 2,       /* the job does not fit the HBM budget (refused before any work) */
+  TC_ECUDA = 3,        /* a CUDA runtime call failed; see tc_last_error */
+  TC_ENOTREADY = 4,    /* tc_poll: the job has not finished yet */
+  TC_ETIMEOUT = 5,     /* tc_wait gave up, or a device-side wait hit its limit */
+  TC_EBUSY = 6,        /* the request queue is full */
+  TC_ECANCELLED = 7,   /* the job was cancelled */
+  TC_EINTERNAL = 8     /* a device-side consistency check failed */
+} tc_status;
+
+typedef enum {
+  TC_FP64 = 0,         /* W built with FP64 tensor-core (DMMA) tiles, FP64 everywhere */
+  TC_SPLIT_BF16 = 1    /* W built from BF16 slices on tcgen05 tensor cores, FP32 accumulation,
+                          FP64 denominator, FP64 per-triplet sums and compensated total */
+} tc_precision;
+
+typedef struct {
+  int device;                /* CUDA device ordinal */
+  size_t hbm_budget_bytes;   /* device bytes the context may hold; 0 = 90% of free memory at init */
+  int default_prec;          /* tc_precision used when a call passes prec < 0 */
+  int default_slices;        /* BF16 slices per operand (2..4) used when a call passes slices <= 0 */
+  int timeout_ms;            /* limit for tc_wait and for device-side waits; 0 = 60000 */
+} tc_options;
+
+typedef struct {
+  const double *ovvv;        /* [o][v][v][v] (ia|bd) */
+  const double *ovoo;        /* [o][v][o][o] (ia|jl) */
+  const double *ovov;        /* [o][v][o][v] (ia|jb) */
+} tc_ints;
+
+typedef struct {
+  double e_t;                /* E_(T) in Eh */
+  double seconds;            /* wall time of the call (tc_energy / tc_energy_dev) or of the job */
+  double tflops_alg;         /* 2 (o^3 v^4 + o^4 v^3) / seconds / 1e12 */
+  int prec;                  /* precision actually used */
+  int slices;                /* BF16 slices per operand (0 for TC_FP64) */
+  int o, v;
+  double queue_seconds;      /* serving: time from tc_submit to the start of its GPU work */
+} tc_result;
+
+/* Create a context on opt->device (opt may be NULL: device 0, defaults).
+ * Allocates nothing large; device memory is reserved per job and reused. */
+tc_status tc_init(tc_ctx **ctx, const tc_options *opt);
+
+/* E_(T) from HOST arrays (Eqs. 1-5).  Blocking.  Copies the inputs to the
+ * device, runs the hot path, returns E_(T) in out->e_t.
+ * prec: tc_precision, or < 0 for the context default.  slices: 2..4 for
+ * TC_SPLIT_BF16, <= 0 for the default; ignored for TC_FP64.
+ * e_ijk (optional, may be NULL): host array [o][o][o] that receives the
+ * weighted contribution of each occupied triplet i >= j >= k at [i][j][k]
+ * (E_(T) is their sum); entries with i < j or j < k are set to 0. */
+tc_status tc_energy(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
+                    const double *t2, const tc_ints *ints, int prec, int slices,
+                    double *e_ijk, tc_result *out);
+
+/* Same as tc_energy with every array a DEVICE pointer (e.g. a PyTorch tensor's
+ * data_ptr on ctx's device), read in place.  stream: a cudaStream_t (NULL =
+ * legacy default stream) on which all work is enqueued; the call returns after
+ * that work completes.  e_ijk_dev (optional): DEVICE array [o][o][o] as above. */
+tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
+                        const double *t2, const tc_ints *ints, int prec, int slices,
+                        double *e_ijk_dev, void *stream, tc_result *out);
+
+/* Device bytes a job of this shape and precision needs besides its inputs
+ * (work tables, partial sums, BF16 slices).  Pure host arithmetic. */
+size_t tc_workspace_bytes(int o, int v, int prec, int slices);
+
+/* Human-readable name of a status. */
+const char *tc_status_str(tc_status s);
+
+/* Text of the last failure recorded on ctx ("" if none). */
+const char *tc_last_error(tc_ctx *ctx);
+
+/* Release everything the context holds.  ctx may be NULL. */
+void tc_finalize(tc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */
