@@ -1,0 +1,156 @@
+"""Python binding of libtc (include/tc.h): argument marshalling only.
+
+Every step of the (T) computation runs in the CUDA library; this module loads
+``libtc.so`` (built in-tree by ``paper_2512_01055_gb300.build``) and converts
+numpy arrays / torch tensors into the pointers and sizes of the C ABI.  There
+is no fallback: if the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ENOTREADY, TC_ETIMEOUT, TC_EBUSY, TC_ECANCELLED, TC_EINTERNAL = range(9)
+TC_FP64, TC_SPLIT_BF16 = 0, 1
+
+#: Every symbol include/tc.h declares (the CPU test checks the library exports them).
+EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
+           "tc_last_error", "tc_finalize")
+
+
+class tc_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("default_prec", ctypes.c_int), ("default_slices", ctypes.c_int),
+                ("timeout_ms", ctypes.c_int)]
+
+
+class tc_ints(ctypes.Structure):
+    _fields_ = [("ovvv", ctypes.c_void_p), ("ovoo", ctypes.c_void_p), ("ovov", ctypes.c_void_p)]
+
+
+class tc_result(ctypes.Structure):
+    _fields_ = [("e_t", ctypes.c_double), ("seconds", ctypes.c_double), ("tflops_alg", ctypes.c_double),
+                ("prec", ctypes.c_int), ("slices", ctypes.c_int), ("o", ctypes.c_int), ("v", ctypes.c_int),
+                ("queue_seconds", ctypes.c_double), ("kernel_seconds", ctypes.c_double),
+                ("prep_seconds", ctypes.c_double), ("n_items", ctypes.c_longlong),
+                ("launches", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_str(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtc.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with `python -m paper_2512_01055_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.tc_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(tc_options)]
+    lib.tc_init.restype = i
+    lib.tc_energy.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(tc_ints), i, i, vp, ctypes.POINTER(tc_result)]
+    lib.tc_energy.restype = i
+    lib.tc_energy_dev.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(tc_ints), i, i, vp, vp,
+                                  ctypes.POINTER(tc_result)]
+    lib.tc_energy_dev.restype = i
+    lib.tc_workspace_bytes.argtypes = [i, i, i, i]
+    lib.tc_workspace_bytes.restype = sz
+    lib.tc_status_str.argtypes = [i]
+    lib.tc_status_str.restype = ctypes.c_char_p
+    lib.tc_last_error.argtypes = [vp]
+    lib.tc_last_error.restype = ctypes.c_char_p
+    lib.tc_finalize.argtypes = [vp]
+    lib.tc_finalize.restype = None
+    del d, dp
+    _lib = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    return load().tc_status_str(s).decode()
+
+
+# ---------------------------------------------------------------------------
+# Same-named thin wrappers
+# ---------------------------------------------------------------------------
+
+def tc_init(device: int = 0, hbm_budget_bytes: int = 0, default_prec: int = TC_FP64,
+            default_slices: int = 3, timeout_ms: int = 0) -> ctypes.c_void_p:
+    lib = load()
+    ctx = ctypes.c_void_p()
+    opt = tc_options(device, hbm_budget_bytes, default_prec, default_slices, timeout_ms)
+    s = lib.tc_init(ctypes.byref(ctx), ctypes.byref(opt))
+    if s != TC_OK:
+        raise TcError(s, "tc_init failed")
+    return ctx
+
+
+def tc_finalize(ctx) -> None:
+    load().tc_finalize(ctx)
+
+
+def tc_last_error(ctx) -> str:
+    return load().tc_last_error(ctx).decode()
+
+
+def tc_workspace_bytes(o: int, v: int, prec: int = TC_FP64, slices: int = 0) -> int:
+    return int(load().tc_workspace_bytes(o, v, prec, slices))
+
+
+def _ptr_np(a):
+    import numpy as np
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("host arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data
+
+
+def _ptr_dev(t):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+    return t.data_ptr()
+
+
+def _check(ctx, s):
+    if s != TC_OK:
+        raise TcError(s, tc_last_error(ctx))
+
+
+def tc_energy(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices=0, e_ijk=None) -> tc_result:
+    """E_(T) from host numpy arrays (layouts of include/tc.h).  e_ijk: optional [o,o,o] float64 output."""
+    ints = tc_ints(_ptr_np(ovvv), _ptr_np(ovoo), _ptr_np(ovov))
+    res = tc_result()
+    s = load().tc_energy(ctx, o, v, _ptr_np(eps), _ptr_np(t1), _ptr_np(t2), ctypes.byref(ints), prec, slices,
+                         _ptr_np(e_ijk), ctypes.byref(res))
+    _check(ctx, s)
+    return res
+
+
+def tc_energy_dev(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices=0, e_ijk=None,
+                  stream=None) -> tc_result:
+    """E_(T) from device torch tensors read in place; ``stream``: a torch.cuda.Stream or None (current)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ints = tc_ints(_ptr_dev(ovvv), _ptr_dev(ovoo), _ptr_dev(ovov))
+    res = tc_result()
+    s = load().tc_energy_dev(ctx, o, v, _ptr_dev(eps), _ptr_dev(t1), _ptr_dev(t2), ctypes.byref(ints), prec,
+                             slices, _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(res))
+    _check(ctx, s)
+    return res

@@ -1,0 +1,355 @@
+// C ABI of the (T) library (include/tc.h): argument checks, HBM admission,
+// device workspace reuse, work tables, launches and the final read-back.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+#include "tc_internal.cuh"
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) { cudaFree(p); p = nullptr; cap = 0; }
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes; else p = nullptr;
+    return e;
+  }
+  void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {            // byte offsets inside the per-job workspace
+  size_t partial, e_trip, out, counter, total;
+};
+
+}  // namespace
+
+struct tc_ctx {
+  int device = 0;
+  size_t budget = 0;
+  int default_prec = TC_FP64;
+  int default_slices = 3;
+  int timeout_ms = 60000;
+  int num_sms = 0;
+  std::mutex mu;
+  std::string err;
+  cudaStream_t stream = nullptr;
+  DevBuf ws;                 // work tables + partials, reused across calls
+  DevBuf tables;             // triplet and orbit tables of the last shape
+  int tab_o = -1, tab_v = -1, tab_nt = -1;
+  DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies
+  double *host_out = nullptr;                               // pinned read-back slot
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing
+};
+
+namespace {
+
+tc_status fail(tc_ctx *ctx, tc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return s;
+}
+
+#define TC_CUDA(ctx, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, TC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                      \
+  } while (0)
+
+tc::Dims make_dims(int o, int v, int nt) {
+  tc::Dims d{};
+  d.o = o;
+  d.v = v;
+  d.nt = nt;
+  d.ntiles = (v + nt - 1) / nt;
+  const long long T = d.ntiles;
+  d.n_trip = (int)((long long)o * (o + 1) * (o + 2) / 6 - o);
+  d.n_orb = (int)(T * (T + 1) * (T + 2) / 6);
+  const long long pairs = (long long)d.n_trip * d.n_orb;
+  const long long target = 4LL << 20;   // at most ~4M partials
+  d.orb_per_item = (int)std::max<long long>(1, (pairs + target - 1) / target);
+  d.items_per_trip = (d.n_orb + d.orb_per_item - 1) / d.orb_per_item;
+  d.n_items = (long long)d.n_trip * d.items_per_trip;
+  return d;
+}
+
+Layout make_layout(const tc::Dims &d) {
+  Layout L{};
+  size_t off = 0;
+  L.partial = off; off = align256(off + sizeof(double) * (size_t)std::max<long long>(1, d.n_items));
+  L.e_trip = off;  off = align256(off + sizeof(double) * (size_t)std::max(1, d.n_trip));
+  L.out = off;     off = align256(off + 4 * sizeof(double));
+  L.counter = off; off = align256(off + 2 * sizeof(unsigned));
+  L.total = off;
+  return L;
+}
+
+size_t table_bytes(const tc::Dims &d) {
+  return align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) + sizeof(int4) * (size_t)std::max(1, d.n_orb);
+}
+
+tc_status ensure_tables(tc_ctx *ctx, const tc::Dims &d, cudaStream_t st, const int4 **trip, const int4 **orb) {
+  const size_t tb = table_bytes(d);
+  if (!(ctx->tab_o == d.o && ctx->tab_v == d.v && ctx->tab_nt == d.nt && ctx->tables.cap >= tb)) {
+    std::vector<int4> h(tb / sizeof(int4) + 1);
+    int4 *ht = h.data();
+    int n = 0;
+    for (int i = 0; i < d.o; ++i)
+      for (int j = 0; j <= i; ++j)
+        for (int k = 0; k <= j; ++k) {
+          if (i == k) continue;                       // i == j == k: zero contribution
+          ht[n++] = make_int4(i, j, k, 2 - (i == j) - (j == k));
+        }
+    int4 *ho = ht + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) / sizeof(int4);
+    int m = 0;
+    for (int P = 0; P < d.ntiles; ++P)
+      for (int Q = 0; Q <= P; ++Q)
+        for (int R = 0; R <= Q; ++R) ho[m++] = make_int4(P, Q, R, 0);
+    if (n != d.n_trip || m != d.n_orb) return fail(ctx, TC_EINTERNAL, "work table size mismatch");
+    TC_CUDA(ctx, ctx->tables.ensure(tb));
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->tables.p, ht, tb, cudaMemcpyHostToDevice, st));
+    TC_CUDA(ctx, cudaStreamSynchronize(st));
+    ctx->tab_o = d.o; ctx->tab_v = d.v; ctx->tab_nt = d.nt;
+  }
+  *trip = (const int4 *)ctx->tables.p;
+  *orb = (const int4 *)((char *)ctx->tables.p + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)));
+  return TC_OK;
+}
+
+tc_status check_args(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
+                     const tc_ints *ints, int *prec, int *slices) {
+  if (!ctx) return TC_EINVAL;
+  if (o <= 0 || v <= 0) return fail(ctx, TC_EINVAL, "o and v must be positive (o=%d v=%d)", o, v);
+  if ((long long)o * v * v * v > (1LL << 40)) return fail(ctx, TC_EINVAL, "o*v^3 too large");
+  if (!eps || !t1 || !t2 || !ints || !ints->ovvv || !ints->ovoo || !ints->ovov)
+    return fail(ctx, TC_EINVAL, "NULL input array");
+  if (*prec < 0) *prec = ctx->default_prec;
+  if (*prec != TC_FP64 && *prec != TC_SPLIT_BF16) return fail(ctx, TC_EINVAL, "unknown precision %d", *prec);
+  if (*prec == TC_SPLIT_BF16) {
+    if (*slices <= 0) *slices = ctx->default_slices;
+    if (*slices < 2 || *slices > 4) return fail(ctx, TC_EINVAL, "slices must be 2, 3 or 4 (got %d)", *slices);
+    return fail(ctx, TC_EINVAL, "split-precision path not available in this build");
+  } else {
+    *slices = 0;
+  }
+  return TC_OK;
+}
+
+double alg_flops(int o, int v) {
+  const double O = o, V = v;
+  return 2.0 * (O * O * O * V * V * V * V + O * O * O * O * V * V * V);
+}
+
+// The hot path on device-resident inputs.  Caller holds ctx->mu.
+tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, int slices, double *e_ijk_dev,
+                     cudaStream_t st, tc_result *out) {
+  (void)slices;
+  const int nt = tc::fp64_tile();
+  const tc::Dims d = make_dims(o, v, nt);
+  const Layout L = make_layout(d);
+  const size_t need = L.total + table_bytes(d);
+  if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "workspace %zu B exceeds budget %zu B", need, ctx->budget);
+  const int4 *trip = nullptr, *orb = nullptr;
+  tc_status s = ensure_tables(ctx, d, st, &trip, &orb);
+  if (s != TC_OK) return s;
+  TC_CUDA(ctx, ctx->ws.ensure(L.total));
+  char *base = (char *)ctx->ws.p;
+  tc::Work w{};
+  w.trip = trip;
+  w.orb = orb;
+  w.partial = (double *)(base + L.partial);
+  w.counter = (unsigned *)(base + L.counter);
+  w.err = (int *)(base + L.counter + sizeof(unsigned));
+  double *e_trip = (double *)(base + L.e_trip);
+  double *dout = (double *)(base + L.out);
+  TC_CUDA(ctx, cudaMemsetAsync(w.counter, 0, 2 * sizeof(unsigned), st));
+  if (e_ijk_dev) TC_CUDA(ctx, cudaMemsetAsync(e_ijk_dev, 0, sizeof(double) * (size_t)o * o * o, st));
+  if (d.n_items > 0) {
+    int per_sm = 0;
+    TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
+    long long grid = (long long)ctx->num_sms * per_sm;
+    grid = std::min<long long>(grid, d.n_items);
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+    TC_CUDA(ctx, tc::launch_fp64(d, in, w, (int)grid, st));
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+  }
+  TC_CUDA(ctx, tc::launch_reduce(d, w, e_trip, e_ijk_dev, dout, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out + 2, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(ctx, cudaStreamSynchronize(st));
+  int errflag = 0;
+  std::memcpy(&errflag, ctx->host_out + 2, sizeof(int));
+  if (errflag != 0) return fail(ctx, TC_EINTERNAL, "device error flag %d", errflag);
+  out->e_t = ctx->host_out[0];
+  if (d.n_items > 0) {
+    float ms = 0.f;
+    TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+    out->kernel_seconds = 1e-3 * ms;
+  }
+  out->n_items = d.n_items;
+  out->launches = (d.n_items > 0 ? 1 : 0) + (d.n_trip > 0 ? 1 : 0) + 1;
+  out->prec = prec;
+  out->slices = (prec == TC_FP64) ? 0 : slices;
+  out->o = o;
+  out->v = v;
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tc_status_str(tc_status s) {
+  switch (s) {
+    case TC_OK: return "TC_OK";
+    case TC_EINVAL: return "TC_EINVAL";
+    case TC_ENOMEM: return "TC_ENOMEM";
+    case TC_ECUDA: return "TC_ECUDA";
+    case TC_ENOTREADY: return "TC_ENOTREADY";
+    case TC_ETIMEOUT: return "TC_ETIMEOUT";
+    case TC_EBUSY: return "TC_EBUSY";
+    case TC_ECANCELLED: return "TC_ECANCELLED";
+    case TC_EINTERNAL: return "TC_EINTERNAL";
+  }
+  return "TC_UNKNOWN";
+}
+
+const char *tc_last_error(tc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+size_t tc_workspace_bytes(int o, int v, int prec, int slices) {
+  (void)prec; (void)slices;
+  if (o <= 0 || v <= 0) return 0;
+  const tc::Dims d = make_dims(o, v, tc::fp64_tile());
+  return make_layout(d).total + table_bytes(d);
+}
+
+tc_status tc_init(tc_ctx **out, const tc_options *opt) {
+  if (!out) return TC_EINVAL;
+  *out = nullptr;
+  tc_ctx *ctx = new (std::nothrow) tc_ctx();
+  if (!ctx) return TC_ENOMEM;
+  if (opt) {
+    ctx->device = opt->device;
+    ctx->budget = opt->hbm_budget_bytes;
+    ctx->default_prec = opt->default_prec;
+    ctx->default_slices = opt->default_slices > 0 ? opt->default_slices : 3;
+    ctx->timeout_ms = opt->timeout_ms > 0 ? opt->timeout_ms : 60000;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ctx->device < 0 || ctx->device >= ndev) {
+    delete ctx;
+    return TC_ECUDA;
+  }
+  if (cudaSetDevice(ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void **)&ctx->host_out, 4 * sizeof(double)) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess ||
+      cudaEventCreate(&ctx->ev[2]) != cudaSuccess || cudaEventCreate(&ctx->ev[3]) != cudaSuccess) {
+    delete ctx;
+    return TC_ECUDA;
+  }
+  if (ctx->budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = (size_t)(0.9 * (double)fr);
+  }
+  *out = ctx;
+  return TC_OK;
+}
+
+void tc_finalize(tc_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->ws.release();
+  ctx->tables.release();
+  ctx->in_eps.release(); ctx->in_t1.release(); ctx->in_t2.release();
+  ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();
+  if (ctx->host_out) cudaFreeHost(ctx->host_out);
+  for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
+                        const tc_ints *ints, int prec, int slices, double *e_ijk_dev, void *stream,
+                        tc_result *out) {
+  if (!ctx || !out) return TC_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  tc_status s = check_args(ctx, o, v, eps, t1, t2, ints, &prec, &slices);
+  if (s != TC_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  TC_CUDA(ctx, cudaSetDevice(ctx->device));
+  tc::Inputs in{eps, t1, t2, ints->ovvv, ints->ovoo, ints->ovov};
+  std::memset(out, 0, sizeof *out);
+  s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, (cudaStream_t)stream, out);
+  if (s != TC_OK) return s;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out->tflops_alg = alg_flops(o, v) / std::max(out->seconds, 1e-12) / 1e12;
+  return TC_OK;
+}
+
+tc_status tc_energy(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
+                    const tc_ints *ints, int prec, int slices, double *e_ijk, tc_result *out) {
+  if (!ctx || !out) return TC_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  tc_status s = check_args(ctx, o, v, eps, t1, t2, ints, &prec, &slices);
+  if (s != TC_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  TC_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t n_eps = (size_t)o + v, n_t1 = (size_t)o * v, n_t2 = (size_t)o * o * v * v;
+  const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
+  const size_t in_bytes = sizeof(double) * (n_eps + n_t1 + n_t2 + n_ovvv + n_ovoo + n_ovov + (size_t)o * o * o);
+  if (in_bytes + tc_workspace_bytes(o, v, prec, slices) > ctx->budget)
+    return fail(ctx, TC_ENOMEM, "job needs %zu B, budget %zu B", in_bytes + tc_workspace_bytes(o, v, prec, slices),
+                ctx->budget);
+  cudaStream_t st = ctx->stream;
+  TC_CUDA(ctx, ctx->in_eps.ensure(sizeof(double) * (n_eps + (size_t)o * o * o)));
+  TC_CUDA(ctx, ctx->in_t1.ensure(sizeof(double) * n_t1));
+  TC_CUDA(ctx, ctx->in_t2.ensure(sizeof(double) * n_t2));
+  TC_CUDA(ctx, ctx->in_ovvv.ensure(sizeof(double) * n_ovvv));
+  TC_CUDA(ctx, ctx->in_ovoo.ensure(sizeof(double) * n_ovoo));
+  TC_CUDA(ctx, ctx->in_ovov.ensure(sizeof(double) * n_ovov));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_eps.p, eps, sizeof(double) * n_eps, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t1.p, t1, sizeof(double) * n_t1, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t2.p, t2, sizeof(double) * n_t2, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovvv.p, ints->ovvv, sizeof(double) * n_ovvv, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovoo.p, ints->ovoo, sizeof(double) * n_ovoo, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovov.p, ints->ovov, sizeof(double) * n_ovov, cudaMemcpyHostToDevice, st));
+  tc::Inputs in{(const double *)ctx->in_eps.p, (const double *)ctx->in_t1.p, (const double *)ctx->in_t2.p,
+                (const double *)ctx->in_ovvv.p, (const double *)ctx->in_ovoo.p, (const double *)ctx->in_ovov.p};
+  double *e_ijk_dev = e_ijk ? (double *)ctx->in_eps.p + n_eps : nullptr;
+  std::memset(out, 0, sizeof *out);
+  s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
+  if (s != TC_OK) return s;
+  if (e_ijk) {
+    TC_CUDA(ctx, cudaMemcpyAsync(e_ijk, e_ijk_dev, sizeof(double) * (size_t)o * o * o, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(ctx, cudaStreamSynchronize(st));
+  }
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out->tflops_alg = alg_flops(o, v) / std::max(out->seconds, 1e-12) / 1e12;
+  return TC_OK;
+}
+
+}  // extern "C"
