@@ -114,6 +114,35 @@ tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const doub
                         const double *t2, const tc_ints *ints, int prec, int slices,
                         double *e_ijk_dev, void *stream, tc_result *out);
 
+/* Size of the library's static device scratch array used by
+ * tc_energy_dev_noalloc (held on every GPU that loads the library). */
+#define TC_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+
+/* FP64 E_(T) for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this entry point exists for code that runs where it may not
+ * call cudaMalloc -- inside a host runtime that owns every device allocation
+ * (fixed pools, embedded solvers, plugins), or where a new allocation could
+ * fail or fragment memory mid-run.
+ *
+ * Same computation and input layouts as tc_energy_dev with prec = TC_FP64, but
+ * no context: it runs on the current device and allocates nothing (no
+ * cudaMalloc/cudaFree, no allocating library call).  Its scratch -- work
+ * tables, partial sums, the work counter -- lives in one static device array
+ * of TC_NOALLOC_SCRATCH_BYTES, shared by every call.
+ *   e_t_dev    DEVICE pointer to one double that receives E_(T) (required).
+ *   e_ijk_dev  optional DEVICE array [o][o][o] of per-triplet contributions.
+ *   stream     cudaStream_t (NULL = legacy default stream).  The call only
+ *              enqueues work; results are valid once that stream reaches them.
+ *   errbuf     optional buffer (errlen bytes) for a message on failure.
+ * Returns TC_ENOMEM, without enqueuing anything, when the job's scratch would
+ * exceed TC_NOALLOC_SCRATCH_BYTES (roughly: more than ~2.5e5 tile orbits).
+ * The first call on a device looks up the array's device address and sets
+ * the kernel's shared-memory limit; make that call before any stream capture.
+ * Calls whose GPU work overlaps race on the shared array: serialise them. */
+tc_status tc_energy_dev_noalloc(int o, int v, const double *eps, const double *t1,
+                                const double *t2, const tc_ints *ints, double *e_t_dev,
+                                double *e_ijk_dev, void *stream, char *errbuf, size_t errlen);
+
 /* Device bytes a job of this shape and precision needs besides its inputs
  * (work tables, partial sums, BF16 slices).  Pure host arithmetic. */
 size_t tc_workspace_bytes(int o, int v, int prec, int slices);

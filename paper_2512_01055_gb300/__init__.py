@@ -18,7 +18,10 @@ TC_FP64, TC_SPLIT_BF16 = 0, 1
 
 #: Every symbol include/tc.h declares (the CPU test checks the library exports them).
 EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
-           "tc_last_error", "tc_finalize")
+           "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc")
+
+#: TC_NOALLOC_SCRATCH_BYTES of include/tc.h
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class tc_options(ctypes.Structure):
@@ -73,6 +76,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_last_error.restype = ctypes.c_char_p
     lib.tc_finalize.argtypes = [vp]
     lib.tc_finalize.restype = None
+    lib.tc_energy_dev_noalloc.argtypes = [i, i, vp, vp, vp, ctypes.POINTER(tc_ints), vp, vp, vp,
+                                          ctypes.c_char_p, sz]
+    lib.tc_energy_dev_noalloc.restype = i
     del d, dp
     _lib = lib
     return lib
@@ -154,3 +160,22 @@ def tc_energy_dev(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices
                              slices, _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(res))
     _check(ctx, s)
     return res
+
+
+def tc_energy_dev_noalloc(o, v, eps, t1, t2, ovvv, ovoo, ovov, e_t, e_ijk=None, stream=None) -> None:
+    """FP64 E_(T) into the device tensor ``e_t`` (one float64) without any device allocation.
+
+    For callers that may not allocate device memory: scratch lives in the
+    library's static device array (NOALLOC_SCRATCH_BYTES).  Only enqueues work
+    on ``stream`` (default: torch's current stream); calls that overlap on the
+    GPU race on the shared array.
+    """
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ints = tc_ints(_ptr_dev(ovvv), _ptr_dev(ovoo), _ptr_dev(ovov))
+    buf = ctypes.create_string_buffer(256)
+    s = load().tc_energy_dev_noalloc(o, v, _ptr_dev(eps), _ptr_dev(t1), _ptr_dev(t2), ctypes.byref(ints),
+                                     _ptr_dev(e_t), _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), buf, 256)
+    if s != TC_OK:
+        raise TcError(s, buf.value.decode())
