@@ -46,6 +46,7 @@ struct tc_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   DevBuf ws;                 // work tables + partials, reused across calls
+  DevBuf ws_split;           // BF16 slices and FP32 copies of the split path
   DevBuf tables;             // triplet and orbit tables of the last shape
   int tab_o = -1, tab_v = -1, tab_nt = -1;
   DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies
@@ -145,7 +146,7 @@ tc_status check_args(tc_ctx *ctx, int o, int v, const double *eps, const double 
   if (*prec == TC_SPLIT_BF16) {
     if (*slices <= 0) *slices = ctx->default_slices;
     if (*slices < 2 || *slices > 4) return fail(ctx, TC_EINVAL, "slices must be 2, 3 or 4 (got %d)", *slices);
-    return fail(ctx, TC_EINVAL, "split-precision path not available in this build");
+    if (o > 255) return fail(ctx, TC_EINVAL, "split path supports o <= 255 (got %d)", o);
   } else {
     *slices = 0;
   }
@@ -160,16 +161,18 @@ double alg_flops(int o, int v) {
 // The hot path on device-resident inputs.  Caller holds ctx->mu.
 tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, int slices, double *e_ijk_dev,
                      cudaStream_t st, tc_result *out) {
-  (void)slices;
-  const int nt = tc::fp64_tile();
+  const bool split = (prec == TC_SPLIT_BF16);
+  const int nt = split ? tc::split_tile() : tc::fp64_tile();
   const tc::Dims d = make_dims(o, v, nt);
   const Layout L = make_layout(d);
-  const size_t need = L.total + table_bytes(d);
+  const tc::SplitLayout SL = split ? tc::split_layout(o, v, slices) : tc::SplitLayout{};
+  const size_t need = L.total + table_bytes(d) + SL.total;
   if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "workspace %zu B exceeds budget %zu B", need, ctx->budget);
   const int4 *trip = nullptr, *orb = nullptr;
   tc_status s = ensure_tables(ctx, d, st, &trip, &orb);
   if (s != TC_OK) return s;
   TC_CUDA(ctx, ctx->ws.ensure(L.total));
+  if (split) TC_CUDA(ctx, ctx->ws_split.ensure(SL.total));
   char *base = (char *)ctx->ws.p;
   tc::Work w{};
   w.trip = trip;
@@ -181,30 +184,50 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   double *dout = (double *)(base + L.out);
   TC_CUDA(ctx, cudaMemsetAsync(w.counter, 0, 2 * sizeof(unsigned), st));
   if (e_ijk_dev) TC_CUDA(ctx, cudaMemsetAsync(e_ijk_dev, 0, sizeof(double) * (size_t)o * o * o, st));
-  if (d.n_items > 0) {
-    int per_sm = 0;
-    TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
-    long long grid = (long long)ctx->num_sms * per_sm;
-    grid = std::min<long long>(grid, d.n_items);
-    TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
-    TC_CUDA(ctx, tc::launch_fp64(d, in, w, (int)grid, st));
-    TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+  int launches = 1;                                      // reduce_total
+  if (split) {
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
+    TC_CUDA(ctx, tc::launch_split_prep(d, slices, in, ctx->ws_split.p, SL, st));
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
+    launches += 6;
   }
+  if (d.n_items > 0) {
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+    if (split) {
+      TC_CUDA(ctx, tc::launch_split(d, slices, in, ctx->ws_split.p, SL, w, ctx->num_sms, st));
+    } else {
+      int per_sm = 0;
+      TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
+      long long grid = (long long)ctx->num_sms * per_sm;
+      grid = std::min<long long>(grid, d.n_items);
+      TC_CUDA(ctx, tc::launch_fp64(d, in, w, (int)grid, st));
+    }
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+    launches += 1;
+  }
+  if (d.n_trip > 0) launches += 1;                       // reduce_triplets
   TC_CUDA(ctx, tc::launch_reduce(d, w, e_trip, e_ijk_dev, dout, st));
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out + 2, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TC_CUDA(ctx, cudaStreamSynchronize(st));
   int errflag = 0;
   std::memcpy(&errflag, ctx->host_out + 2, sizeof(int));
-  if (errflag != 0) return fail(ctx, TC_EINTERNAL, "device error flag %d", errflag);
+  if (errflag != 0)
+    return fail(ctx, (errflag >= 11 && errflag <= 15) ? TC_ETIMEOUT : TC_EINTERNAL,
+                "device-side wait gave up (code %d)", errflag);
   out->e_t = ctx->host_out[0];
   if (d.n_items > 0) {
     float ms = 0.f;
     TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
     out->kernel_seconds = 1e-3 * ms;
   }
+  if (split) {
+    float ms = 0.f;
+    TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
+    out->prep_seconds = 1e-3 * ms;
+  }
   out->n_items = d.n_items;
-  out->launches = (d.n_items > 0 ? 1 : 0) + (d.n_trip > 0 ? 1 : 0) + 1;
+  out->launches = launches;
   out->prec = prec;
   out->slices = (prec == TC_FP64) ? 0 : slices;
   out->o = o;
@@ -234,10 +257,11 @@ const char *tc_status_str(tc_status s) {
 const char *tc_last_error(tc_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 size_t tc_workspace_bytes(int o, int v, int prec, int slices) {
-  (void)prec; (void)slices;
   if (o <= 0 || v <= 0) return 0;
-  const tc::Dims d = make_dims(o, v, tc::fp64_tile());
-  return make_layout(d).total + table_bytes(d);
+  const bool split = (prec == TC_SPLIT_BF16);
+  if (split && slices <= 0) slices = 3;
+  const tc::Dims d = make_dims(o, v, split ? tc::split_tile() : tc::fp64_tile());
+  return make_layout(d).total + table_bytes(d) + (split ? tc::split_layout(o, v, slices).total : 0);
 }
 
 tc_status tc_init(tc_ctx **out, const tc_options *opt) {
@@ -281,6 +305,7 @@ void tc_finalize(tc_ctx *ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->ws.release();
+  ctx->ws_split.release();
   ctx->tables.release();
   ctx->in_eps.release(); ctx->in_t1.release(); ctx->in_t2.release();
   ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();

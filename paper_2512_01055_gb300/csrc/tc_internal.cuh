@@ -60,4 +60,17 @@ cudaError_t fp64_blocks_per_sm(int *n);
 cudaError_t launch_reduce(const Dims &d, const Work &w, double *e_trip, double *e_ijk, double *out,
                           cudaStream_t st);
 
+// Split-precision path (tc_split.cu): byte offsets of the BF16 slices and FP32
+// copies inside its workspace.
+struct SplitLayout {
+  int vpad, opad;                          // row pitches (elements), multiples of 8
+  size_t ovvv, t2, t2h, ovoo, t1f, ovovf;  // offsets
+  size_t total;
+};
+int split_tile();
+SplitLayout split_layout(int o, int v, int S);
+cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st);
+cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, const Work &w,
+                         int num_sms, cudaStream_t st);
+
 }  // namespace tc

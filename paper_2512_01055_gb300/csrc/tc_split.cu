@@ -1,0 +1,651 @@
+// Split-precision path: W (Eqs. 2, 5) from BF16 slices on the tcgen05 tensor
+// cores (FP32 accumulation in TMEM), V (Eq. 3) in FP32, D (Fig. 4 sign) and
+// its reciprocal in FP64, per-item energy sums in FP64.
+//
+// Slices.  Every FP64 operand x is written as s BF16 numbers x_0 + ... + x_{s-1}
+// with x_0 = bf16(x) and x_p = bf16(x - x_0 - ... - x_{p-1}) (round to
+// nearest; the FP64 residual is exact), the splitting used to emulate higher
+// precision with BF16 products (Henry, Tang, Heinecke, ARITH 2019; an
+// Ozaki-style error-free-ish expansion with per-element exponents).  A product
+// is approximated by the slice pairs with p + q < s, grouped by level L = p + q.
+//
+// GEMM tiles.  Virtual tiles have edge 16.  A "job" is one A tile of 256 rows
+// (pairs of two virtual tiles) and one or two B panels of 16 rows:
+//   particle:  A = (x a | b f) = ovvv[x][a][b][f],  B = t2[y][z][c][f],  K = v
+//   hole:      A = t2[l][z][a][b] (re-laid out with l last),  B = -(x c | y l),  K = o
+// For each K step of 16 the MMA warp issues, per 128-row half, one MMA per A
+// slice p with the B slices 0 .. s-1-p stacked along N, so each A slice is read
+// from shared memory once and lands in its level's TMEM columns.  The drain
+// warps add the levels (smallest first) and scatter the 256 x 16 (x panels)
+// results into the orbit's W blocks in shared memory with the job's index
+// permutation.  After all jobs of an orbit, the same warps evaluate the Eq. 1
+// bracket over the orbit's canonical points (as in the FP64 path) and
+// accumulate FP64 partials.
+//
+// Warp roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 owns TMEM
+// and lane 0 issues MMAs, warps 2-5 drain TMEM and run the energy epilogue.
+// Every mbarrier wait is bounded; on expiry the kernel records an error code,
+// lets every role leave its loop, waits (bounded) for its own copies and MMAs
+// and frees TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int NT = 16;                    // virtual tile edge
+constexpr int KC = 16;                    // K per pipeline stage (32-byte rows, 32B swizzle)
+constexpr int A_SLICE_BYTES = 256 * KC * 2;
+constexpr int B_PANEL_BYTES = NT * KC * 2;
+constexpr int MAXS = 4;
+constexpr int MAX_STAGES = 8;
+constexpr int THREADS = 192;
+constexpr int EPI_THREADS = 128;
+constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
+constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
+constexpr int W_BYTES = 6 * WBLK * 4;
+constexpr int MAX_JOBS = 72;
+constexpr long long WAIT_LIMIT = 1LL << 26;
+
+constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL = 13,
+              ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
+
+struct Job {
+  uint8_t kind;          // 0 particle, 1 hole
+  uint8_t np;            // panels (1 or 2)
+  uint8_t aocc;          // occupied index value of the A tile (x for particle, z for hole)
+  uint8_t pad0;
+  int16_t ta, tb;        // A tile pair: rows (a, b) with a in tile ta, b in tile tb
+  int16_t ptile[2];      // panel tile
+  uint8_t pocc0[2];      // particle: y of t2[y][z]; hole: x of ovoo[x][c][y]
+  uint8_t pocc1[2];      // particle: z;               hole: y
+  uint8_t blk[2];        // W block
+  uint8_t hi[2], lo[2], col[2];   // W positions of row/16, row%16, panel column
+};
+
+struct SplitParams {
+  Dims d;
+  int S;
+  int stages;
+  int kch_p, kch_h;      // K steps of particle / hole jobs
+  const float *t1f, *ovovf;
+  const double *eps;
+  Work w;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// Bounded wait; gives up early when another role has aborted.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_try(a, parity)) return true;
+    if ((it & 255) == 255) {
+      if (*abort_flag) return false;
+      __nanosleep(128);
+    }
+  }
+  *abort_flag = 1;
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load5(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 32-byte swizzle, 8-row groups 256 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+  d |= (uint64_t)((8 * KC * 2) >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)6 << 61;                          // 32-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dcol, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(dcol), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
+
+// Distinct tile block holding each formal permutation of the orbit's tile triple.
+__device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6]) {
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    blk[s] = s;
+    for (int s2 = 0; s2 < s; ++s2)
+      if (blk[s] == s && tl[perm3(s2, 0)] == tl[perm3(s, 0)] && tl[perm3(s2, 1)] == tl[perm3(s, 1)] &&
+          tl[perm3(s2, 2)] == tl[perm3(s, 2)])
+        blk[s] = s2;
+  }
+}
+
+// The GEMM jobs of one (triplet, orbit): for every distinct block s and every
+// permutation u of Eq. 5, one particle and one hole product; products that
+// share an A tile are paired into one job (at most two panels).
+__device__ int build_jobs(const int occ[3], const int tl[3], Job *jobs) {
+  int blk[6];
+  orbit_blocks(tl, blk);
+  int n = 0;
+  for (int kind = 0; kind < 2; ++kind) {
+    const int first = n;
+    for (int s = 0; s < 6; ++s) {
+      if (blk[s] != s) continue;
+      int T[3];
+      for (int p = 0; p < 3; ++p) T[p] = tl[perm3(s, p)];
+      for (int u = 0; u < 6; ++u) {
+        const int u0 = perm3(u, 0), u1 = perm3(u, 1), u2 = perm3(u, 2);
+        int aocc, ta, tb, ptile, po0, po1, hi, lo, col;
+        if (kind == 0) {   // sum_f (x p | q f) t2[z][y][r][f]: rows (u0, u1), column u2
+          aocc = occ[u0]; ta = T[u0]; tb = T[u1];
+          ptile = T[u2]; po0 = occ[u2]; po1 = occ[u1];
+          hi = u0; lo = u1; col = u2;
+        } else {           // -sum_l (x p | y l) t2[l][z][q][r]: rows (u1, u2), column u0
+          aocc = occ[u2]; ta = T[u1]; tb = T[u2];
+          ptile = T[u0]; po0 = occ[u0]; po1 = occ[u1];
+          hi = u1; lo = u2; col = u0;
+        }
+        int j = -1;
+        for (int q = first; q < n; ++q)
+          if (jobs[q].np == 1 && jobs[q].aocc == aocc && jobs[q].ta == ta && jobs[q].tb == tb) { j = q; break; }
+        int slot = 1;
+        if (j < 0) {
+          j = n++;
+          jobs[j].kind = (uint8_t)kind; jobs[j].np = 0; jobs[j].aocc = (uint8_t)aocc;
+          jobs[j].ta = (int16_t)ta; jobs[j].tb = (int16_t)tb;
+          slot = 0;
+        }
+        jobs[j].np = (uint8_t)(slot + 1);
+        jobs[j].ptile[slot] = (int16_t)ptile;
+        jobs[j].pocc0[slot] = (uint8_t)po0; jobs[j].pocc1[slot] = (uint8_t)po1;
+        jobs[j].blk[slot] = (uint8_t)s;
+        jobs[j].hi[slot] = (uint8_t)hi; jobs[j].lo[slot] = (uint8_t)lo; jobs[j].col[slot] = (uint8_t)col;
+      }
+    }
+  }
+  return n;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constant__ CUtensorMap m_t2,
+                const __grid_constant__ CUtensorMap m_t2h, const __grid_constant__ CUtensorMap m_ovoo,
+                const SplitParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = P.S;
+  const int stage_bytes = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
+  float *Wsm = (float *)(sm + P.stages * stage_bytes);
+
+  __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
+  __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+  __shared__ int epi_ok;
+  __shared__ double red[4];
+  __shared__ Job epi_jobs[MAX_JOBS];
+  __shared__ int epi_nj;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Dims &d = P.d;
+  const int o = d.o, v = d.v;
+
+  if (tid == 0) {
+    for (int s = 0; s < P.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accfull_bar[b], 1); mbar_init(&accempty_bar[b], 1); }
+    mbar_init(&teardown_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base_sh)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (warp >= 2) {
+    for (int e = tid - 64; e < 6 * WBLK; e += EPI_THREADS) Wsm[e] = 0.f;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tmem_base_sh;
+  const int bufcols = 2 * S * 32;
+
+  Job jobs[MAX_JOBS];
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+        const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+        const int4 tr = P.w.trip[t];
+        const int occ[3] = {tr.x, tr.y, tr.z};
+        const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
+        for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
+          const int4 og = P.w.orb[ob];
+          const int tl[3] = {og.x, og.y, og.z};
+          const int nj = build_jobs(occ, tl, jobs);
+          for (int jb = 0; ok && jb < nj; ++jb) {
+            const Job &J = jobs[jb];
+            const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
+            const uint32_t bytes = (uint32_t)S * (A_SLICE_BYTES + J.np * B_PANEL_BYTES);
+            for (int kc = 0; kc < nk; ++kc) {
+              if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_EMPTY)) { ok = false; break; }
+              unsigned char *sA = sm + stage * stage_bytes;
+              unsigned char *sB = sA + S * A_SLICE_BYTES;
+              mbar_expect_tx(&full_bar[stage], bytes);
+              const int k0 = kc * KC;
+              for (int p = 0; p < S; ++p) {
+                if (J.kind == 0) tma_load5(sA + p * A_SLICE_BYTES, &m_ovvv, k0, J.tb * NT, J.ta * NT, J.aocc, p, &full_bar[stage]);
+                else             tma_load5(sA + p * A_SLICE_BYTES, &m_t2h, k0, J.tb * NT, J.ta * NT, J.aocc, p, &full_bar[stage]);
+              }
+              for (int q = 0; q < S; ++q)
+                for (int pn = 0; pn < J.np; ++pn) {
+                  unsigned char *dst = sB + (q * J.np + pn) * B_PANEL_BYTES;
+                  if (J.kind == 0) tma_load5(dst, &m_t2, k0, J.ptile[pn] * NT, J.pocc1[pn], J.pocc0[pn], q, &full_bar[stage]);
+                  else             tma_load5(dst, &m_ovoo, k0, J.pocc1[pn], J.ptile[pn] * NT, J.pocc0[pn], q, &full_bar[stage]);
+                }
+              if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+            }
+          }
+        }
+      }
+      // wait for every copy this thread issued (bounded) before the CTA may exit
+      for (int s = 0; s < P.stages; ++s) {
+        // the most recent use of stage s had parity (phase ^ 1) if s >= stage, else phase
+        const uint32_t par = (s >= stage) ? (phase ^ 1u) : phase;
+        const uint32_t a = smem_u32(&full_bar[s]);
+        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, par); ++it) {
+          if ((it & 255) == 255) __nanosleep(128);
+          if (it == WAIT_LIMIT - 1) atomicCAS(P.w.err, 0, ERR_TIMEOUT_TEARDOWN);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0, abuf = 0;
+      uint32_t phase = 0, aphase = 0;
+      bool ok = true;
+      for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+        const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+        const int4 tr = P.w.trip[t];
+        const int occ[3] = {tr.x, tr.y, tr.z};
+        const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
+        for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
+          const int4 og = P.w.orb[ob];
+          const int tl[3] = {og.x, og.y, og.z};
+          const int nj = build_jobs(occ, tl, jobs);
+          for (int jb = 0; ok && jb < nj; ++jb) {
+            const Job &J = jobs[jb];
+            const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
+            if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dbase = tbase + (uint32_t)(abuf * bufcols);
+            for (int kc = 0; kc < nk; ++kc) {
+              if (!mbar_wait(&full_bar[stage], phase, &abort_flag, P.w.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t sA = smem_u32(sm + stage * stage_bytes);
+              const uint32_t sB = sA + S * A_SLICE_BYTES;
+              const uint64_t bd = sdesc(sB);
+              for (int h = 0; h < 2; ++h)
+                for (int a = 0; a < S; ++a) {
+                  const int N = (S - a) * J.np * NT;
+                  const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + h * (A_SLICE_BYTES / 2));
+                  const uint32_t dcol = dbase + (uint32_t)(h * S * 32 + a * J.np * NT);
+                  mma_bf16(dcol, ad, bd, idesc(128, N), (kc > 0 || a > 0) ? 1u : 0u);
+                }
+              mma_commit(&empty_bar[stage]);
+              if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+            }
+            if (!ok) break;
+            mma_commit(&accfull_bar[abuf]);
+            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+          }
+        }
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(&teardown_bar);
+      const uint32_t a = smem_u32(&teardown_bar);
+      for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, 0); ++it) {
+        if ((it & 255) == 255) __nanosleep(128);
+        if (it == WAIT_LIMIT - 1) atomicCAS(P.w.err, 0, ERR_TIMEOUT_TEARDOWN);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ drain + energy epilogue
+    const int et = tid - 64;                  // 0 .. 127
+    const int quarter = warp & 3;             // TMEM lane quarter this warp may access
+    const int lrow = 32 * quarter + lane;     // row within a 128-row half
+    int abuf = 0;
+    uint32_t aphase = 0;
+    bool ok = true;
+    for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+      const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+      const int4 tr = P.w.trip[t];
+      const int occ[3] = {tr.x, tr.y, tr.z};
+      const double eijk = __ldg(P.eps + occ[0]) + __ldg(P.eps + occ[1]) + __ldg(P.eps + occ[2]);
+      double acc = 0.0;
+      const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
+      for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
+        const int4 og = P.w.orb[ob];
+        const int tl[3] = {og.x, og.y, og.z};
+        if (et == 0) epi_nj = build_jobs(occ, tl, epi_jobs);
+        epi_bar();
+        const int nj = epi_nj;
+        for (int jb = 0; jb < nj; ++jb) {
+          const Job &J = epi_jobs[jb];
+          if (et == 0)
+            epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, P.w.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
+          epi_bar();
+          if (!epi_ok) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dbase = tbase + (uint32_t)(abuf * bufcols) + ((uint32_t)(32 * quarter) << 16);
+          for (int h = 0; h < 2; ++h) {
+            const int row = h * 128 + lrow;
+            const int rhi = row >> 4, rlo = row & 15;
+            for (int pn = 0; pn < J.np; ++pn) {
+              float sum[16], lv[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) sum[j] = 0.f;
+              for (int L = S - 1; L >= 0; --L) {    // smallest level first
+                tmem_ld16(dbase + (uint32_t)(h * S * 32 + L * J.np * NT + pn * NT), lv);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) sum[j] += lv[j];
+              }
+              int lc[3];
+              lc[J.hi[pn]] = rhi;
+              lc[J.lo[pn]] = rlo;
+              float *Wb = Wsm + J.blk[pn] * WBLK;
+              const int cstride = (J.col[pn] == 0) ? WX : (J.col[pn] == 1 ? WY : 1);
+              lc[J.col[pn]] = 0;
+              float *base = Wb + lc[0] * WX + lc[1] * WY + lc[2];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) base[j * cstride] += sum[j];
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          epi_bar();                             // all loads and W updates of this job are done
+          if (et == 0) mbar_arrive(&accempty_bar[abuf]);
+          if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+        }
+        if (!ok) break;
+
+        // energy over the canonical points a >= b >= c of the orbit
+        int blk[6];
+        orbit_blocks(tl, blk);
+        for (int pr = et; pr < NT * NT; pr += EPI_THREADS) {
+          const int la = pr >> 4, lb = pr & 15;
+          const int ga = tl[0] * NT + la, gb = tl[1] * NT + lb;
+          if (ga >= v || gb >= v || ga < gb) continue;
+          const double dab = eijk - (__ldg(P.eps + o + ga) + __ldg(P.eps + o + gb));
+          for (int lcc = 0; lcc < NT; ++lcc) {
+            const int gc = tl[2] * NT + lcc;
+            if (gc >= v || gb < gc) continue;
+            const int l3[3] = {la, lb, lcc};
+            const int g[3] = {ga, gb, gc};
+            float ws[6], vs[6];
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+              const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
+              ws[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
+              const int x = g[p0], y = g[p1], z = g[p2];
+              const float *ov = P.ovovf;
+              vs[s] = __ldg(P.t1f + occ[0] * v + x) * __ldg(ov + ((occ[1] * v + y) * o + occ[2]) * v + z)
+                    + __ldg(P.t1f + occ[1] * v + y) * __ldg(ov + ((occ[0] * v + x) * o + occ[2]) * v + z)
+                    + __ldg(P.t1f + occ[2] * v + z) * __ldg(ov + ((occ[0] * v + x) * o + occ[1]) * v + y);
+            }
+            const float se = ws[0] + ws[3] + ws[4];
+            const float so = ws[1] + ws[2] + ws[5];
+            float sum = 0.f;
+#pragma unroll
+            for (int s = 0; s < 6; ++s) {
+              const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
+              sum = fmaf(ws[s] + vs[s], br, sum);
+            }
+            // FP64 denominator: D = e_i + e_j + e_k - e_a - e_b - e_c and 1/D by one
+            // Newton-Raphson step from the hardware reciprocal estimate.
+            const double D = dab - __ldg(P.eps + o + gc);
+            double r;
+            asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(D));
+            r = fma(r, fma(-D, r, 1.0), r);
+            const double mult = (ga == gc) ? (1.0 / 6.0) : ((ga == gb || gb == gc) ? 0.5 : 1.0);
+            acc = fma((double)sum * mult, r, acc);
+          }
+        }
+        epi_bar();
+        for (int e = et; e < 6 * WBLK; e += EPI_THREADS) Wsm[e] = 0.f;
+        epi_bar();
+      }
+      if (!ok) break;
+      // the item's partial: fixed-order reduction over the 128 epilogue threads
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) red[warp - 2] = acc;
+      epi_bar();
+      if (et == 0) P.w.partial[item] = (red[0] + red[1]) + (red[2] + red[3]);
+      epi_bar();
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tbase), "r"(512));
+  }
+}
+
+// ---------------------------------------------------------------- slicer kernels
+
+template <typename T>
+__device__ __forceinline__ void put_slices(double x, int S, __nv_bfloat16 *dst, long long slice_stride) {
+  double r = x;
+  for (int p = 0; p < S; ++p) {
+    const __nv_bfloat16 b = __double2bfloat16(r);
+    dst[p * slice_stride] = b;
+    r -= (double)__bfloat162float(b);
+  }
+}
+
+// rows of length n (contiguous) -> rows of pitch `pitch`, negated if neg
+__global__ void slice_rows(const double *__restrict__ in, long long rows, int n, int pitch, int S, int neg,
+                           __nv_bfloat16 *__restrict__ out) {
+  const long long total = rows * n;
+  const long long sstride = rows * pitch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / n;
+    const int c = (int)(e - r * n);
+    const double x = neg ? -in[e] : in[e];
+    put_slices<double>(x, S, out + r * pitch + c, sstride);
+  }
+}
+
+// t2h[z][a][b][l] = t2[l][z][a][b]
+__global__ void slice_t2h(const double *__restrict__ t2, int o, int v, int opad, int S, __nv_bfloat16 *__restrict__ out) {
+  const long long total = (long long)o * o * v * v;                 // input order (l, z, a, b)
+  const long long sstride = (long long)o * v * v * opad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long zab = e % ((long long)o * v * v);
+    const int l = (int)(e / ((long long)o * v * v));
+    put_slices<double>(t2[e], S, out + zab * opad + l, sstride);
+  }
+}
+
+__global__ void to_f32(const double *__restrict__ in, long long n, float *__restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 5-D BF16 map, dims innermost first; strides in elements for dims 1..4.
+bool make_map(CUtensorMap *m, void *base, const long long dims[5], const long long strides_el[4], const int box[5]) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t gd[5], gs[4];
+  cuuint32_t bx[5], es[5];
+  for (int i = 0; i < 5; ++i) { gd[i] = (cuuint64_t)dims[i]; bx[i] = (cuuint32_t)box[i]; es[i] = 1; }
+  for (int i = 0; i < 4; ++i) gs[i] = (cuuint64_t)strides_el[i] * 2;
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+int stages_for(int S) {
+  const int stage_bytes = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
+  const int budget = 227 * 1024 - W_BYTES - 1024 - 256;
+  int st = budget / stage_bytes;
+  if (st > MAX_STAGES) st = MAX_STAGES;
+  return st;
+}
+
+size_t smem_for(int S) {
+  return (size_t)stages_for(S) * S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES) + W_BYTES + 1024;
+}
+
+}  // namespace
+
+int split_tile() { return NT; }
+
+SplitLayout split_layout(int o, int v, int S) {
+  SplitLayout L{};
+  L.vpad = (v + 7) / 8 * 8;
+  L.opad = (o + 7) / 8 * 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~(size_t)255; return r; };
+  L.ovvv = take((size_t)S * o * v * v * L.vpad * 2);
+  L.t2 = take((size_t)S * o * o * v * L.vpad * 2);
+  L.t2h = take((size_t)S * o * v * v * L.opad * 2);
+  L.ovoo = take((size_t)S * o * v * o * L.opad * 2);
+  L.t1f = take((size_t)o * v * 4);
+  L.ovovf = take((size_t)o * v * o * v * 4);
+  L.total = off;
+  return L;
+}
+
+cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st) {
+  const int o = d.o, v = d.v;
+  char *b = (char *)ws;
+  const int blocks = 152 * 8, thr = 256;
+  slice_rows<<<blocks, thr, 0, st>>>(in.ovvv, (long long)o * v * v, v, L.vpad, S, 0, (__nv_bfloat16 *)(b + L.ovvv));
+  slice_rows<<<blocks, thr, 0, st>>>(in.t2, (long long)o * o * v, v, L.vpad, S, 0, (__nv_bfloat16 *)(b + L.t2));
+  slice_t2h<<<blocks, thr, 0, st>>>(in.t2, o, v, L.opad, S, (__nv_bfloat16 *)(b + L.t2h));
+  slice_rows<<<blocks, thr, 0, st>>>(in.ovoo, (long long)o * v * o, o, L.opad, S, 1, (__nv_bfloat16 *)(b + L.ovoo));
+  to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)o * v, (float *)(b + L.t1f));
+  to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)o * v * o * v, (float *)(b + L.ovovf));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, const Work &w,
+                         int num_sms, cudaStream_t st) {
+  if (S < 2 || S > MAXS) return cudaErrorInvalidValue;
+  const int o = d.o, v = d.v;
+  char *b = (char *)ws;
+  CUtensorMap m_ovvv, m_t2, m_t2h, m_ovoo;
+  {  // ovvv slices [S][o][v][v][vpad]: dims (f, b, a, x, slice)
+    const long long dims[5] = {v, v, v, o, S};
+    const long long str[4] = {L.vpad, (long long)v * L.vpad, (long long)v * v * L.vpad, (long long)o * v * v * L.vpad};
+    const int box[5] = {KC, NT, NT, 1, 1};
+    if (!make_map(&m_ovvv, b + L.ovvv, dims, str, box)) return cudaErrorInvalidValue;
+  }
+  {  // t2 slices [S][o][o][v][vpad]: dims (f, c, z, y, slice)
+    const long long dims[5] = {v, v, o, o, S};
+    const long long str[4] = {L.vpad, (long long)v * L.vpad, (long long)o * v * L.vpad, (long long)o * o * v * L.vpad};
+    const int box[5] = {KC, NT, 1, 1, 1};
+    if (!make_map(&m_t2, b + L.t2, dims, str, box)) return cudaErrorInvalidValue;
+  }
+  {  // t2h slices [S][o][v][v][opad]: dims (l, b, a, z, slice)
+    const long long dims[5] = {o, v, v, o, S};
+    const long long str[4] = {L.opad, (long long)v * L.opad, (long long)v * v * L.opad, (long long)o * v * v * L.opad};
+    const int box[5] = {KC, NT, NT, 1, 1};
+    if (!make_map(&m_t2h, b + L.t2h, dims, str, box)) return cudaErrorInvalidValue;
+  }
+  {  // -ovoo slices [S][o][v][o][opad]: dims (l, y, c, x, slice)
+    const long long dims[5] = {o, o, v, o, S};
+    const long long str[4] = {L.opad, (long long)o * L.opad, (long long)v * o * L.opad, (long long)o * v * o * L.opad};
+    const int box[5] = {KC, 1, NT, 1, 1};
+    if (!make_map(&m_ovoo, b + L.ovoo, dims, str, box)) return cudaErrorInvalidValue;
+  }
+  SplitParams P{};
+  P.d = d;
+  P.S = S;
+  P.stages = stages_for(S);
+  P.kch_p = (v + KC - 1) / KC;
+  P.kch_h = (o + KC - 1) / KC;
+  P.t1f = (const float *)(b + L.t1f);
+  P.ovovf = (const float *)(b + L.ovovf);
+  P.eps = in.eps;
+  P.w = w;
+  const size_t smem = smem_for(S);
+  cudaError_t e = cudaFuncSetAttribute(tc_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  long long grid = num_sms;
+  if (grid > d.n_items) grid = d.n_items;
+  if (grid < 1) return cudaSuccess;
+  tc_split_kernel<<<(int)grid, THREADS, smem, st>>>(m_ovvv, m_t2, m_t2h, m_ovoo, P);
+  return cudaGetLastError();
+}
+
+}  // namespace tc

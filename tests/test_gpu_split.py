@@ -1,0 +1,109 @@
+"""Split-precision (BF16 slices on tcgen05) path against the CPU oracle.
+
+Tolerances.  s BF16 slices carry about 8s significant bits of every operand
+and the products accumulate in FP32, so W carries a relative error of order
+2^-24 for s >= 3 (FP32 accumulation dominates) and 2^-16 for s = 2.  E_T is a
+sum of W^2-like terms, so its relative error is of the same order.  The
+stated bound is |dE| <= 1e-6 Eh; the synthetic inputs have |E_T| far above a
+physical size, so it is applied as |dE| <= 1e-6 max(1 Eh, |E_T|), and
+literally (absolute 1e-6 Eh) on the physical-scale twin whose amplitudes are
+scaled by a power of two mu (E_T scales exactly by mu^2).
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2512_01055_gb300 as tc
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+SPLIT = tc.TC_SPLIT_BF16
+REL = {2: 1e-4, 3: 1e-6, 4: 1e-6}
+
+
+def rel_bound(s, e_ref):
+    return REL[s] * max(1.0, abs(e_ref))
+
+
+@pytest.mark.parametrize("s", [2, 3, 4])
+def test_tiny_workload_all_slice_counts(s):
+    job = synth.workload_job("tiny_o6_v36")
+    r, e_ijk = gpu_util.energy_dev(job, prec=SPLIT, slices=s, want_trip=True)
+    ref = oracle.energy_by_triplets(job)
+    err = abs(r.e_t - ref)
+    print(f"s={s} E={r.e_t:.12e} ref={ref:.12e} |dE|={err:.3e} rel={err / abs(ref):.3e}")
+    assert r.prec == SPLIT and r.slices == s
+    assert err <= rel_bound(s, ref)
+    scale = max(abs(oracle.triplet_energy(job, *t)) for t in oracle.triplet_list(job.o))
+    for t in oracle.triplet_list(job.o):
+        assert abs(e_ijk[t] - oracle.triplet_energy(job, *t)) <= 10 * REL[s] * scale, t
+
+
+@pytest.mark.parametrize("o,v,seed", [(3, 5, 1), (4, 17, 2), (5, 33, 3), (2, 47, 4), (7, 20, 5), (3, 64, 6)])
+def test_ragged_shapes(o, v, seed):
+    """Tiles of 16 with ragged last tiles, coincident-tile orbits, i=j / j=k triplets, K not a multiple of 16."""
+    job = synth.make_job(o, v, seed)
+    r, e_ijk = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
+    ref = oracle.energy_by_triplets(job)
+    print(f"o={o} v={v} |dE|/|E|={abs(r.e_t - ref) / abs(ref):.3e}")
+    assert abs(r.e_t - ref) <= rel_bound(3, ref)
+
+
+def test_physical_scale_twin_absolute_bound():
+    """Amplitudes scaled by mu = 2^-4 so |E_T| ~ 0.1 Eh: the literal 1e-6 Eh bound applies."""
+    job = synth.workload_job("tiny_o6_v36")
+    mu = 2.0 ** -4
+    twin = dataclasses.replace(job, t1=job.t1 * mu, t2=job.t2 * mu)
+    ref = oracle.energy_by_triplets(job) * mu * mu          # exact scaling law (pinned on the oracle)
+    for s in (3, 4):
+        r, _ = gpu_util.energy_dev(twin, prec=SPLIT, slices=s)
+        print(f"twin s={s} E={r.e_t:.12e} ref={ref:.12e} |dE|={abs(r.e_t - ref):.3e}")
+        assert abs(ref) < 1.0
+        assert abs(r.e_t - ref) <= 1e-6
+
+
+@pytest.mark.parametrize("o,v", [(1, 9), (3, 1), (1, 1)])
+def test_degenerate_shapes(o, v):
+    job = synth.make_job(o, v, 13)
+    r, _ = gpu_util.energy_dev(job, prec=SPLIT, slices=3)
+    ref = oracle.energy_eq1(job)
+    if o == 1 or v == 1:
+        assert abs(r.e_t) <= 1e-6 * max(1e-12, abs(r.e_t) + 1.0)
+    assert abs(r.e_t - ref) <= 1e-6
+
+
+def test_split_is_deterministic_and_host_entry_agrees():
+    job = synth.make_job(4, 29, 21)
+    r1, e1 = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
+    r2, e2 = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
+    rh, eh = gpu_util.energy_host(job, prec=SPLIT, slices=3, want_trip=True)
+    assert r1.e_t == r2.e_t == rh.e_t
+    np.testing.assert_array_equal(e1, e2)
+    np.testing.assert_array_equal(e1, eh)
+
+
+def test_split_matches_fp64_path_closely():
+    job = synth.make_job(5, 40, 22)
+    rf, ef = gpu_util.energy_dev(job, prec=tc.TC_FP64, want_trip=True)
+    rs, es = gpu_util.energy_dev(job, prec=SPLIT, slices=4, want_trip=True)
+    assert abs(rs.e_t - rf.e_t) <= 1e-6 * abs(rf.e_t)
+
+
+def test_zero_amplitudes_exact_zero_split():
+    job = synth.make_job(4, 18, 8)
+    job.t1[:] = 0.0
+    job.t2[:] = 0.0
+    r, _ = gpu_util.energy_dev(job, prec=SPLIT, slices=3)
+    assert r.e_t == 0.0
+
+
+def test_invalid_slice_counts():
+    job = synth.make_job(2, 3, 1)
+    for s in (1, 5):
+        with pytest.raises(tc.TcError) as ei:
+            gpu_util.energy_host(job, prec=SPLIT, slices=s)
+        assert ei.value.status == tc.TC_EINVAL
