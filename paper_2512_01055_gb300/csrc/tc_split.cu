@@ -30,6 +30,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -52,18 +54,32 @@ constexpr long long WAIT_LIMIT = 1LL << 26;
 constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL = 13,
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
 
-struct Job {
-  uint8_t kind;          // 0 particle, 1 hole
-  uint8_t np;            // panels (1 or 2)
-  uint8_t aocc;          // occupied index value of the A tile (x for particle, z for hole)
-  uint8_t pad0;
-  int16_t ta, tb;        // A tile pair: rows (a, b) with a in tile ta, b in tile tb
-  int16_t ptile[2];      // panel tile
-  uint8_t pocc0[2];      // particle: y of t2[y][z]; hole: x of ovoo[x][c][y]
-  uint8_t pocc1[2];      // particle: z;               hole: y
-  uint8_t blk[2];        // W block
-  uint8_t hi[2], lo[2], col[2];   // W positions of row/16, row%16, panel column
+// One GEMM job of an (occupied pattern, tile pattern) template.  Every field
+// is a position (0, 1, 2) into the triplet's occupied indices occ[] or the
+// orbit's tile indices tl[], so one template serves every triplet and orbit
+// with the same equality pattern (i > j > k, i = j > k, i > j = k) x
+// (P > Q > R, P = Q > R, P > Q = R, P = Q = R).
+struct TJob {
+  uint8_t kind;              // 0 particle, 1 hole
+  uint8_t np;                // panels (1 or 2)
+  uint8_t apos;              // A tile occupied index: occ[apos]
+  uint8_t tapos, tbpos;      // A rows (a, b): a in tile tl[tapos], b in tile tl[tbpos]
+  uint8_t pad;
+  uint8_t ptpos[2];          // panel tile tl[ptpos]
+  uint8_t p0pos[2];          // particle: y of t2[y][z]; hole: x of (x c|y l)
+  uint8_t p1pos[2];          // particle: z;              hole: y
+  uint8_t blk[2];            // W block (distinct permutation index of the orbit)
+  uint8_t hi[2], lo[2], col[2];   // W positions receiving row/16, row%16 and the panel column
 };
+constexpr int N_PATTERNS = 12;
+__constant__ TJob c_tjobs[N_PATTERNS][MAX_JOBS];
+__constant__ int c_ntjobs[N_PATTERNS];
+
+__host__ __device__ __forceinline__ int pattern_id(const int occ[3], const int tl[3]) {
+  const int op = (occ[0] == occ[1]) ? 1 : ((occ[1] == occ[2]) ? 2 : 0);
+  const int tp = (tl[0] == tl[1] && tl[1] == tl[2]) ? 3 : ((tl[0] == tl[1]) ? 1 : ((tl[1] == tl[2]) ? 2 : 0));
+  return op * 4 + tp;
+}
 
 struct SplitParams {
   Dims d;
@@ -153,7 +169,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
 
 // Distinct tile block holding each formal permutation of the orbit's tile triple.
-__device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6]) {
+__host__ __device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6]) {
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     blk[s] = s;
@@ -164,10 +180,13 @@ __device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6]) {
   }
 }
 
-// The GEMM jobs of one (triplet, orbit): for every distinct block s and every
-// permutation u of Eq. 5, one particle and one hole product; products that
-// share an A tile are paired into one job (at most two panels).
-__device__ int build_jobs(const int occ[3], const int tl[3], Job *jobs) {
+// The GEMM jobs of one (triplet, orbit) pattern: for every distinct block s and
+// every permutation u of Eq. 5, one particle and one hole product; products
+// that share an A tile are paired into one job (at most two panels).  Built on
+// the host from representative index values; positions are stored.
+int host_build_template(const int occ[3], const int tl[3], TJob *jobs) {
+  auto opos = [&](int val) { return val == occ[0] ? 0 : (val == occ[1] ? 1 : 2); };
+  auto tpos = [&](int val) { return val == tl[0] ? 0 : (val == tl[1] ? 1 : 2); };
   int blk[6];
   orbit_blocks(tl, blk);
   int n = 0;
@@ -191,17 +210,24 @@ __device__ int build_jobs(const int occ[3], const int tl[3], Job *jobs) {
         }
         int j = -1;
         for (int q = first; q < n; ++q)
-          if (jobs[q].np == 1 && jobs[q].aocc == aocc && jobs[q].ta == ta && jobs[q].tb == tb) { j = q; break; }
+          if (jobs[q].np == 1 && occ[jobs[q].apos] == aocc && tl[jobs[q].tapos] == ta && tl[jobs[q].tbpos] == tb) {
+            j = q;
+            break;
+          }
         int slot = 1;
         if (j < 0) {
           j = n++;
-          jobs[j].kind = (uint8_t)kind; jobs[j].np = 0; jobs[j].aocc = (uint8_t)aocc;
-          jobs[j].ta = (int16_t)ta; jobs[j].tb = (int16_t)tb;
+          jobs[j] = TJob{};
+          jobs[j].kind = (uint8_t)kind;
+          jobs[j].apos = (uint8_t)opos(aocc);
+          jobs[j].tapos = (uint8_t)tpos(ta);
+          jobs[j].tbpos = (uint8_t)tpos(tb);
           slot = 0;
         }
         jobs[j].np = (uint8_t)(slot + 1);
-        jobs[j].ptile[slot] = (int16_t)ptile;
-        jobs[j].pocc0[slot] = (uint8_t)po0; jobs[j].pocc1[slot] = (uint8_t)po1;
+        jobs[j].ptpos[slot] = (uint8_t)tpos(ptile);
+        jobs[j].p0pos[slot] = (uint8_t)opos(po0);
+        jobs[j].p1pos[slot] = (uint8_t)opos(po1);
         jobs[j].blk[slot] = (uint8_t)s;
         jobs[j].hi[slot] = (uint8_t)hi; jobs[j].lo[slot] = (uint8_t)lo; jobs[j].col[slot] = (uint8_t)col;
       }
@@ -210,15 +236,15 @@ __device__ int build_jobs(const int occ[3], const int tl[3], Job *jobs) {
   return n;
 }
 
+template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constant__ CUtensorMap m_t2,
                 const __grid_constant__ CUtensorMap m_t2h, const __grid_constant__ CUtensorMap m_ovoo,
                 const SplitParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int S = P.S;
-  const int stage_bytes = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
-  float *Wsm = (float *)(sm + P.stages * stage_bytes);
+  constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
+  float *Wsm = (float *)(sm + P.stages * STAGE_BYTES);
 
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar;
@@ -226,8 +252,6 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
   __shared__ volatile int abort_flag;
   __shared__ int epi_ok;
   __shared__ double red[4];
-  __shared__ Job epi_jobs[MAX_JOBS];
-  __shared__ int epi_nj;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Dims &d = P.d;
@@ -251,53 +275,63 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_base_sh;
-  const int bufcols = 2 * S * 32;
-
-  Job jobs[MAX_JOBS];
+  constexpr int BUFCOLS = 2 * S * 32;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      bool ok = true;
-      for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
-        const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
-        const int4 tr = P.w.trip[t];
-        const int occ[3] = {tr.x, tr.y, tr.z};
-        const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
-        for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
-          const int4 og = P.w.orb[ob];
-          const int tl[3] = {og.x, og.y, og.z};
-          const int nj = build_jobs(occ, tl, jobs);
-          for (int jb = 0; ok && jb < nj; ++jb) {
-            const Job &J = jobs[jb];
-            const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
-            const uint32_t bytes = (uint32_t)S * (A_SLICE_BYTES + J.np * B_PANEL_BYTES);
-            for (int kc = 0; kc < nk; ++kc) {
-              if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_EMPTY)) { ok = false; break; }
-              unsigned char *sA = sm + stage * stage_bytes;
-              unsigned char *sB = sA + S * A_SLICE_BYTES;
-              mbar_expect_tx(&full_bar[stage], bytes);
-              const int k0 = kc * KC;
-              for (int p = 0; p < S; ++p) {
-                if (J.kind == 0) tma_load5(sA + p * A_SLICE_BYTES, &m_ovvv, k0, J.tb * NT, J.ta * NT, J.aocc, p, &full_bar[stage]);
-                else             tma_load5(sA + p * A_SLICE_BYTES, &m_t2h, k0, J.tb * NT, J.ta * NT, J.aocc, p, &full_bar[stage]);
-              }
-              for (int q = 0; q < S; ++q)
-                for (int pn = 0; pn < J.np; ++pn) {
-                  unsigned char *dst = sB + (q * J.np + pn) * B_PANEL_BYTES;
-                  if (J.kind == 0) tma_load5(dst, &m_t2, k0, J.ptile[pn] * NT, J.pocc1[pn], J.pocc0[pn], q, &full_bar[stage]);
-                  else             tma_load5(dst, &m_ovoo, k0, J.pocc1[pn], J.ptile[pn] * NT, J.pocc0[pn], q, &full_bar[stage]);
-                }
-              if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+    // ------------------------------------------------------------ TMA producer (whole warp)
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+      const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+      const int4 tr = P.w.trip[t];
+      const int occ[3] = {tr.x, tr.y, tr.z};
+      const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
+      for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
+        const int4 og = P.w.orb[ob];
+        const int tl[3] = {og.x, og.y, og.z};
+        const int pid = pattern_id(occ, tl);
+        const int nj = c_ntjobs[pid];
+        for (int jb = 0; ok && jb < nj; ++jb) {
+          const TJob J = c_tjobs[pid][jb];
+          const int np = J.np;
+          const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
+          const uint32_t bytes = (uint32_t)S * (A_SLICE_BYTES + np * B_PANEL_BYTES);
+          const int aocc = occ[J.apos], ta = tl[J.tapos], tb = tl[J.tbpos];
+          // lane 1 + (q * np + pn) loads B slice q of panel pn
+          const int bl = lane - 1, bq = bl / 2, bpn = bl % 2;
+          const bool bload = lane >= 1 && bq < S && bpn < np;
+          int bt = 0, b0 = 0, b1 = 0;
+          if (bload) { bt = tl[J.ptpos[bpn]]; b0 = occ[J.p0pos[bpn]]; b1 = occ[J.p1pos[bpn]]; }
+          for (int kc = 0; kc < nk; ++kc) {
+            int got = 1;
+            if (lane == 0) {
+              got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
+              if (got) mbar_expect_tx(&full_bar[stage], bytes);
             }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) { ok = false; break; }
+            unsigned char *sA = sm + stage * STAGE_BYTES;
+            unsigned char *sB = sA + S * A_SLICE_BYTES;
+            const int k0 = kc * KC;
+            if (lane == 0) {                       // all S slices of the A tile in one copy
+              if (J.kind == 0) tma_load5(sA, &m_ovvv, k0, tb * NT, ta * NT, aocc, 0, &full_bar[stage]);
+              else             tma_load5(sA, &m_t2h, k0, tb * NT, ta * NT, aocc, 0, &full_bar[stage]);
+            } else if (bload) {
+              unsigned char *dst = sB + (bq * np + bpn) * B_PANEL_BYTES;
+              if (J.kind == 0) tma_load5(dst, &m_t2, k0, bt * NT, b1, b0, bq, &full_bar[stage]);
+              else             tma_load5(dst, &m_ovoo, k0, b1, bt * NT, b0, bq, &full_bar[stage]);
+            }
+            __syncwarp();
+            if (++stage == P.stages) { stage = 0; phase ^= 1u; }
           }
         }
       }
-      // wait for every copy this thread issued (bounded) before the CTA may exit
+    }
+    // wait for every copy this warp issued (bounded) before the CTA may exit
+    if (lane == 0) {
       for (int s = 0; s < P.stages; ++s) {
-        // the most recent use of stage s had parity (phase ^ 1) if s >= stage, else phase
+        // the most recent use of stage s had parity phase if s < stage, else phase ^ 1
         const uint32_t par = (s >= stage) ? (phase ^ 1u) : phase;
         const uint32_t a = smem_u32(&full_bar[s]);
         for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, par); ++it) {
@@ -306,6 +340,7 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
         }
       }
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -320,25 +355,26 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
         for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
           const int4 og = P.w.orb[ob];
           const int tl[3] = {og.x, og.y, og.z};
-          const int nj = build_jobs(occ, tl, jobs);
+          const int pid = pattern_id(occ, tl);
+          const int nj = c_ntjobs[pid];
           for (int jb = 0; ok && jb < nj; ++jb) {
-            const Job &J = jobs[jb];
-            const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
+            const int np = c_tjobs[pid][jb].np;
+            const int nk = c_tjobs[pid][jb].kind == 0 ? P.kch_p : P.kch_h;
             if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dbase = tbase + (uint32_t)(abuf * bufcols);
+            const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS);
             for (int kc = 0; kc < nk; ++kc) {
               if (!mbar_wait(&full_bar[stage], phase, &abort_flag, P.w.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t sA = smem_u32(sm + stage * stage_bytes);
-              const uint32_t sB = sA + S * A_SLICE_BYTES;
-              const uint64_t bd = sdesc(sB);
+              const uint32_t sA = smem_u32(sm + stage * STAGE_BYTES);
+              const uint64_t bd = sdesc(sA + S * A_SLICE_BYTES);
+#pragma unroll
               for (int h = 0; h < 2; ++h)
+#pragma unroll
                 for (int a = 0; a < S; ++a) {
-                  const int N = (S - a) * J.np * NT;
                   const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + h * (A_SLICE_BYTES / 2));
-                  const uint32_t dcol = dbase + (uint32_t)(h * S * 32 + a * J.np * NT);
-                  mma_bf16(dcol, ad, bd, idesc(128, N), (kc > 0 || a > 0) ? 1u : 0u);
+                  const uint32_t dcol = dbase + (uint32_t)(h * S * 32 + a * np * NT);
+                  mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > 0 || a > 0) ? 1u : 0u);
                 }
               mma_commit(&empty_bar[stage]);
               if (++stage == P.stages) { stage = 0; phase ^= 1u; }
@@ -376,39 +412,45 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
       for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
         const int4 og = P.w.orb[ob];
         const int tl[3] = {og.x, og.y, og.z};
-        if (et == 0) epi_nj = build_jobs(occ, tl, epi_jobs);
-        epi_bar();
-        const int nj = epi_nj;
+        const int pid = pattern_id(occ, tl);
+        const int nj = c_ntjobs[pid];
         for (int jb = 0; jb < nj; ++jb) {
-          const Job &J = epi_jobs[jb];
+          const TJob J = c_tjobs[pid][jb];
           if (et == 0)
             epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, P.w.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
           epi_bar();
           if (!epi_ok) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dbase = tbase + (uint32_t)(abuf * bufcols) + ((uint32_t)(32 * quarter) << 16);
-          for (int h = 0; h < 2; ++h) {
-            const int row = h * 128 + lrow;
-            const int rhi = row >> 4, rlo = row & 15;
-            for (int pn = 0; pn < J.np; ++pn) {
-              float sum[16], lv[16];
+          const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS) + ((uint32_t)(32 * quarter) << 16);
+          const int np = J.np;
+          // The two panels of a job may update the same W elements (coincident tiles put
+          // both products in one block with different orientations), so panel 1 starts
+          // only after every thread has finished panel 0.
 #pragma unroll
-              for (int j = 0; j < 16; ++j) sum[j] = 0.f;
-              for (int L = S - 1; L >= 0; --L) {    // smallest level first
-                tmem_ld16(dbase + (uint32_t)(h * S * 32 + L * J.np * NT + pn * NT), lv);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int pn = 0; pn < 2; ++pn) {
+            if (pn >= np) break;
+            if (pn == 1) epi_bar();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) sum[j] += lv[j];
-              }
+            for (int h = 0; h < 2; ++h) {
+              const int row = h * 128 + lrow;
+              const int rhi = row >> 4, rlo = row & 15;
+              float lv[S][16];
+#pragma unroll
+              for (int L = 0; L < S; ++L) tmem_ld16(dbase + (uint32_t)(h * S * 32 + L * np * NT + pn * NT), lv[L]);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
               int lc[3];
               lc[J.hi[pn]] = rhi;
               lc[J.lo[pn]] = rlo;
-              float *Wb = Wsm + J.blk[pn] * WBLK;
-              const int cstride = (J.col[pn] == 0) ? WX : (J.col[pn] == 1 ? WY : 1);
               lc[J.col[pn]] = 0;
-              float *base = Wb + lc[0] * WX + lc[1] * WY + lc[2];
+              const int cstride = (J.col[pn] == 0) ? WX : (J.col[pn] == 1 ? WY : 1);
+              float *base = Wsm + J.blk[pn] * WBLK + lc[0] * WX + lc[1] * WY + lc[2];
 #pragma unroll
-              for (int j = 0; j < 16; ++j) base[j * cstride] += sum[j];
+              for (int j = 0; j < 16; ++j) {
+                float sum = lv[S - 1][j];             // smallest level first
+#pragma unroll
+                for (int L = S - 2; L >= 0; --L) sum += lv[L][j];
+                base[j * cstride] += sum;
+              }
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -565,6 +607,41 @@ size_t smem_for(int S) {
   return (size_t)stages_for(S) * S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES) + W_BYTES + 1024;
 }
 
+template <int S>
+cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &b,
+                          const CUtensorMap &c, const CUtensorMap &dmap, const SplitParams &P) {
+  cudaError_t e = cudaFuncSetAttribute(tc_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(a, b, c, dmap, P);
+  return cudaGetLastError();
+}
+
+// The 12 job templates, built on the host once and copied to constant memory
+// once per device.
+cudaError_t upload_templates(cudaStream_t st) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  static TJob h[N_PATTERNS][MAX_JOBS];
+  static int hn[N_PATTERNS];
+  const int occ_rep[3][3] = {{2, 1, 0}, {1, 1, 0}, {1, 0, 0}};
+  const int tl_rep[4][3] = {{2, 1, 0}, {1, 1, 0}, {1, 0, 0}, {0, 0, 0}};
+  for (int op = 0; op < 3; ++op)
+    for (int tp = 0; tp < 4; ++tp) {
+      const int pid = pattern_id(occ_rep[op], tl_rep[tp]);
+      hn[pid] = host_build_template(occ_rep[op], tl_rep[tp], h[pid]);
+    }
+  e = cudaMemcpyToSymbolAsync(c_tjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ntjobs, hn, sizeof(hn), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
 }  // namespace
 
 int split_tile() { return NT; }
@@ -607,7 +684,7 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
   {  // ovvv slices [S][o][v][v][vpad]: dims (f, b, a, x, slice)
     const long long dims[5] = {v, v, v, o, S};
     const long long str[4] = {L.vpad, (long long)v * L.vpad, (long long)v * v * L.vpad, (long long)o * v * v * L.vpad};
-    const int box[5] = {KC, NT, NT, 1, 1};
+    const int box[5] = {KC, NT, NT, 1, S};   // all S slices in one copy
     if (!make_map(&m_ovvv, b + L.ovvv, dims, str, box)) return cudaErrorInvalidValue;
   }
   {  // t2 slices [S][o][o][v][vpad]: dims (f, c, z, y, slice)
@@ -619,7 +696,7 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
   {  // t2h slices [S][o][v][v][opad]: dims (l, b, a, z, slice)
     const long long dims[5] = {o, v, v, o, S};
     const long long str[4] = {L.opad, (long long)v * L.opad, (long long)v * v * L.opad, (long long)o * v * v * L.opad};
-    const int box[5] = {KC, NT, NT, 1, 1};
+    const int box[5] = {KC, NT, NT, 1, S};   // all S slices in one copy
     if (!make_map(&m_t2h, b + L.t2h, dims, str, box)) return cudaErrorInvalidValue;
   }
   {  // -ovoo slices [S][o][v][o][opad]: dims (l, y, c, x, slice)
@@ -639,12 +716,17 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
   P.eps = in.eps;
   P.w = w;
   const size_t smem = smem_for(S);
-  cudaError_t e = cudaFuncSetAttribute(tc_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = upload_templates(st);
   if (e != cudaSuccess) return e;
   long long grid = num_sms;
   if (grid > d.n_items) grid = d.n_items;
   if (grid < 1) return cudaSuccess;
-  tc_split_kernel<<<(int)grid, THREADS, smem, st>>>(m_ovvv, m_t2, m_t2h, m_ovoo, P);
+  switch (S) {
+    case 2: e = launch_kernel<2>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
+    case 3: e = launch_kernel<3>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
+    default: e = launch_kernel<4>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
+  }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
