@@ -22,8 +22,17 @@
 // bracket over the orbit's canonical points (as in the FP64 path) and
 // accumulate FP64 partials.
 //
-// Warp roles (192 threads): warp 0 lane 0 issues TMA loads, warp 1 owns TMEM
-// and lane 0 issues MMAs, warps 2-5 drain TMEM and run the energy epilogue.
+// Operand images.  The slicer writes every A tile (256 rows x 16 K) and B
+// panel (16 rows x 16 K) of every K block directly in the tensor core's
+// K-major no-swizzle layout (8-row x 16-byte core matrices, the two K halves
+// 128 bytes apart, 8-row groups 256 bytes apart), tile-major with the S slices
+// of a block contiguous.  One pipeline stage is then one contiguous bulk copy
+// (cp.async.bulk) for A and one per B slice, instead of hundreds of 32-byte
+// tensor-map rows per stage.
+//
+// Warp roles (320 threads): warp 0 issues the bulk copies, warp 1 owns TMEM
+// and lane 0 issues MMAs, warps 2-9 (two warpgroups, one per 128-row half of
+// each job) drain TMEM and run the energy epilogue.
 // Every mbarrier wait is bounded; on expiry the kernel records an error code,
 // lets every role leave its loop, waits (bounded) for its own copies and MMAs
 // and frees TMEM.
@@ -43,8 +52,9 @@ constexpr int A_SLICE_BYTES = 256 * KC * 2;
 constexpr int B_PANEL_BYTES = NT * KC * 2;
 constexpr int MAXS = 4;
 constexpr int MAX_STAGES = 8;
-constexpr int THREADS = 192;
-constexpr int EPI_THREADS = 128;
+constexpr int THREADS = 320;
+constexpr int EPI_THREADS = 256;
+constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
 constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
 constexpr int W_BYTES = 6 * WBLK * 4;
@@ -85,7 +95,9 @@ struct SplitParams {
   Dims d;
   int S;
   int stages;
-  int kch_p, kch_h;      // K steps of particle / hole jobs
+  int kch_p, kch_h;      // K blocks (of 16) of particle / hole jobs
+  int T;                 // virtual tiles
+  const unsigned char *imgA_p, *imgA_h, *imgB_p, *imgB_h;   // operand images
   const float *t1f, *ovovf;
   const double *eps;
   Work w;
@@ -125,22 +137,20 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void tma_load5(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
-                                          uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-      :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
-      : "memory");
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 32-byte swizzle, 8-row groups 256 bytes apart.
+// Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows
+// x 16 bytes, the next core matrix along K 128 bytes on, the next 8-row group
+// 256 bytes on.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
-  d |= (uint64_t)((8 * KC * 2) >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)(128 >> 4) << 16;                 // leading byte offset (K direction)
+  d |= (uint64_t)(256 >> 4) << 32;                 // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                          // descriptor version
-  d |= (uint64_t)6 << 61;                          // 32-byte swizzle
-  return d;
+  return d;                                        // swizzle field 0
 }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M x N.
@@ -238,9 +248,7 @@ int host_build_template(const int occ[3], const int tl[3], TJob *jobs) {
 
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constant__ CUtensorMap m_t2,
-                const __grid_constant__ CUtensorMap m_t2h, const __grid_constant__ CUtensorMap m_ovoo,
-                const SplitParams P) {
+tc_split_kernel(const SplitParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
@@ -251,7 +259,7 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   __shared__ int epi_ok;
-  __shared__ double red[4];
+  __shared__ double red[EPI_WARPS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const Dims &d = P.d;
@@ -298,11 +306,18 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
           const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
           const uint32_t bytes = (uint32_t)S * (A_SLICE_BYTES + np * B_PANEL_BYTES);
           const int aocc = occ[J.apos], ta = tl[J.tapos], tb = tl[J.tbpos];
-          // lane 1 + (q * np + pn) loads B slice q of panel pn
+          const int T = P.T;
+          // A image of K block kc: ((aocc*T + ta)*T + tb)*nk + kc, S slices of 8 KB each
+          const unsigned char *srcA = (J.kind == 0 ? P.imgA_p : P.imgA_h) +
+                                      ((size_t)((aocc * T + ta) * T + tb) * nk) * S * A_SLICE_BYTES;
+          // lane 1 + (q * 2 + pn) copies B slice q of panel pn
           const int bl = lane - 1, bq = bl / 2, bpn = bl % 2;
           const bool bload = lane >= 1 && bq < S && bpn < np;
-          int bt = 0, b0 = 0, b1 = 0;
-          if (bload) { bt = tl[J.ptpos[bpn]]; b0 = occ[J.p0pos[bpn]]; b1 = occ[J.p1pos[bpn]]; }
+          const unsigned char *srcB = nullptr;
+          if (bload) {
+            const int bt = tl[J.ptpos[bpn]], b0 = occ[J.p0pos[bpn]], b1 = occ[J.p1pos[bpn]];
+            srcB = (J.kind == 0 ? P.imgB_p : P.imgB_h) + ((size_t)((b0 * o + b1) * T + bt) * nk * S + bq) * B_PANEL_BYTES;
+          }
           for (int kc = 0; kc < nk; ++kc) {
             int got = 1;
             if (lane == 0) {
@@ -313,14 +328,11 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
             if (!got) { ok = false; break; }
             unsigned char *sA = sm + stage * STAGE_BYTES;
             unsigned char *sB = sA + S * A_SLICE_BYTES;
-            const int k0 = kc * KC;
-            if (lane == 0) {                       // all S slices of the A tile in one copy
-              if (J.kind == 0) tma_load5(sA, &m_ovvv, k0, tb * NT, ta * NT, aocc, 0, &full_bar[stage]);
-              else             tma_load5(sA, &m_t2h, k0, tb * NT, ta * NT, aocc, 0, &full_bar[stage]);
+            if (lane == 0) {
+              bulk_load(sA, srcA + (size_t)kc * S * A_SLICE_BYTES, S * A_SLICE_BYTES, &full_bar[stage]);
             } else if (bload) {
-              unsigned char *dst = sB + (bq * np + bpn) * B_PANEL_BYTES;
-              if (J.kind == 0) tma_load5(dst, &m_t2, k0, bt * NT, b1, b0, bq, &full_bar[stage]);
-              else             tma_load5(dst, &m_ovoo, k0, b1, bt * NT, b0, bq, &full_bar[stage]);
+              bulk_load(sB + (bq * np + bpn) * B_PANEL_BYTES, srcB + (size_t)kc * S * B_PANEL_BYTES, B_PANEL_BYTES,
+                        &full_bar[stage]);
             }
             __syncwarp();
             if (++stage == P.stages) { stage = 0; phase ^= 1u; }
@@ -396,9 +408,10 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
     __syncwarp();
   } else {
     // ------------------------------------------------------------ drain + energy epilogue
-    const int et = tid - 64;                  // 0 .. 127
+    const int et = tid - 64;                  // 0 .. 255
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
     const int lrow = 32 * quarter + lane;     // row within a 128-row half
+    const int h = et >> 7;                    // warpgroup -> 128-row half of every job
     int abuf = 0;
     uint32_t aphase = 0;
     bool ok = true;
@@ -430,8 +443,7 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
           for (int pn = 0; pn < 2; ++pn) {
             if (pn >= np) break;
             if (pn == 1) epi_bar();
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            {
               const int row = h * 128 + lrow;
               const int rhi = row >> 4, rlo = row & 15;
               float lv[S][16];
@@ -512,7 +524,12 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
       if (lane == 0) red[warp - 2] = acc;
       epi_bar();
-      if (et == 0) P.w.partial[item] = (red[0] + red[1]) + (red[2] + red[3]);
+      if (et == 0) {
+        double tot = 0.0;
+#pragma unroll
+        for (int wq = 0; wq < EPI_WARPS; ++wq) tot += red[wq];
+        P.w.partial[item] = tot;
+      }
       epi_bar();
     }
   }
@@ -525,74 +542,72 @@ tc_split_kernel(const __grid_constant__ CUtensorMap m_ovvv, const __grid_constan
   }
 }
 
-// ---------------------------------------------------------------- slicer kernels
+// ---------------------------------------------------------------- operand images
 
-template <typename T>
-__device__ __forceinline__ void put_slices(double x, int S, __nv_bfloat16 *dst, long long slice_stride) {
-  double r = x;
-  for (int p = 0; p < S; ++p) {
-    const __nv_bfloat16 b = __double2bfloat16(r);
-    dst[p * slice_stride] = b;
-    r -= (double)__bfloat162float(b);
-  }
-}
-
-// rows of length n (contiguous) -> rows of pitch `pitch`, negated if neg
-__global__ void slice_rows(const double *__restrict__ in, long long rows, int n, int pitch, int S, int neg,
-                           __nv_bfloat16 *__restrict__ out) {
-  const long long total = rows * n;
-  const long long sstride = rows * pitch;
+// One thread per (image, row, K half): reads 8 consecutive K values of one
+// operand row, splits them into S BF16 slices and writes 16 bytes per slice at
+// the row's place in the no-swizzle K-major image.  Rows or K values outside
+// the tensor are zero.
+//   mode 0: A particle  image (x, ta, tb, kb), row (a, b), K = f:  (x a | b f)
+//   mode 1: A hole      image (z, ta, tb, kb), row (a, b), K = l:  t2[l][z][a][b]
+//   mode 2: B particle  image (y, z, tc, kb),  row c,      K = f:  t2[y][z][c][f]
+//   mode 3: B hole      image (x, y, tc, kb),  row c,      K = l:  -(x c | y l)
+__global__ void build_images(int mode, const double *__restrict__ src, int o, int v, int T, int nkb, int S,
+                             unsigned char *__restrict__ out) {
+  const int rows = (mode < 2) ? 256 : 16;
+  const int img_bytes = rows * KC * 2;
+  const long long nimg = (long long)((mode == 0 || mode == 1) ? o * T * T : o * o * T) * nkb;
+  const long long total = nimg * rows * 2;
+  const long long vv = (long long)v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / n;
-    const int c = (int)(e - r * n);
-    const double x = neg ? -in[e] : in[e];
-    put_slices<double>(x, S, out + r * pitch + c, sstride);
-  }
-}
-
-// t2h[z][a][b][l] = t2[l][z][a][b]
-__global__ void slice_t2h(const double *__restrict__ t2, int o, int v, int opad, int S, __nv_bfloat16 *__restrict__ out) {
-  const long long total = (long long)o * o * v * v;                 // input order (l, z, a, b)
-  const long long sstride = (long long)o * v * v * opad;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long zab = e % ((long long)o * v * v);
-    const int l = (int)(e / ((long long)o * v * v));
-    put_slices<double>(t2[e], S, out + zab * opad + l, sstride);
+    const int kh = (int)(e & 1);
+    const int r = (int)((e >> 1) % rows);
+    const long long img = (e >> 1) / rows;
+    const int kb = (int)(img % nkb);
+    const long long rest = img / nkb;                      // (.., .., tile) or (.., tile, tile)
+    double x[8];
+    int k0 = kb * KC + kh * 8;
+    if (mode < 2) {
+      const int tb = (int)(rest % T), ta = (int)((rest / T) % T), xo = (int)(rest / ((long long)T * T));
+      const int a = ta * NT + r / NT, b = tb * NT + r % NT;
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        double val = 0.0;
+        if (mode == 0) { if (a < v && b < v && k < v) val = src[((long long)xo * v + a) * vv + (long long)b * v + k]; }
+        else           { if (a < v && b < v && k < o) val = src[((long long)k * o + xo) * vv + (long long)a * v + b]; }
+        x[q] = val;
+      }
+    } else {
+      const int tc = (int)(rest % T);
+      const long long pair = rest / T;                     // y*o + z  or  x*o + y
+      const int p0 = (int)(pair / o), p1 = (int)(pair % o);
+      const int c = tc * NT + r;
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        double val = 0.0;
+        if (mode == 2) { if (c < v && k < v) val = src[(((long long)p0 * o + p1) * v + c) * v + k]; }
+        else           { if (c < v && k < o) val = -src[(((long long)p0 * v + c) * o + p1) * o + k]; }
+        x[q] = val;
+      }
+    }
+    // position of (row r, K half kh) in the image: core matrix (r/8, kh), row r%8
+    const int off = ((r >> 3) * 2 + kh) * 128 + (r & 7) * 16;
+    unsigned char *base = out + (size_t)img * S * img_bytes + off;
+    for (int p = 0; p < S; ++p) {
+      __align__(16) __nv_bfloat16 b16[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        b16[q] = __double2bfloat16(x[q]);
+        x[q] -= (double)__bfloat162float(b16[q]);        // exact FP64 residual
+      }
+      *(uint4 *)(base + (size_t)p * img_bytes) = *(const uint4 *)b16;
+    }
   }
 }
 
 __global__ void to_f32(const double *__restrict__ in, long long n, float *__restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
-
-// 5-D BF16 map, dims innermost first; strides in elements for dims 1..4.
-bool make_map(CUtensorMap *m, void *base, const long long dims[5], const long long strides_el[4], const int box[5]) {
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return false;
-  cuuint64_t gd[5], gs[4];
-  cuuint32_t bx[5], es[5];
-  for (int i = 0; i < 5; ++i) { gd[i] = (cuuint64_t)dims[i]; bx[i] = (cuuint32_t)box[i]; es[i] = 1; }
-  for (int i = 0; i < 4; ++i) gs[i] = (cuuint64_t)strides_el[i] * 2;
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, gd, gs, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
 }
 
 int stages_for(int S) {
@@ -608,11 +623,10 @@ size_t smem_for(int S) {
 }
 
 template <int S>
-cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const CUtensorMap &a, const CUtensorMap &b,
-                          const CUtensorMap &c, const CUtensorMap &dmap, const SplitParams &P) {
+cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const SplitParams &P) {
   cudaError_t e = cudaFuncSetAttribute(tc_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(a, b, c, dmap, P);
+  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -648,14 +662,15 @@ int split_tile() { return NT; }
 
 SplitLayout split_layout(int o, int v, int S) {
   SplitLayout L{};
-  L.vpad = (v + 7) / 8 * 8;
-  L.opad = (o + 7) / 8 * 8;
+  const long long T = (v + NT - 1) / NT, nkb = (v + KC - 1) / KC, nko = (o + KC - 1) / KC;
+  L.vpad = (int)(T * NT);
+  L.opad = (int)(nko * KC);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~(size_t)255; return r; };
-  L.ovvv = take((size_t)S * o * v * v * L.vpad * 2);
-  L.t2 = take((size_t)S * o * o * v * L.vpad * 2);
-  L.t2h = take((size_t)S * o * v * v * L.opad * 2);
-  L.ovoo = take((size_t)S * o * v * o * L.opad * 2);
+  L.ovvv = take((size_t)o * T * T * nkb * S * A_SLICE_BYTES);     // A particle images
+  L.t2h = take((size_t)o * T * T * nko * S * A_SLICE_BYTES);      // A hole images
+  L.t2 = take((size_t)o * o * T * nkb * S * B_PANEL_BYTES);       // B particle images
+  L.ovoo = take((size_t)o * o * T * nko * S * B_PANEL_BYTES);     // B hole images
   L.t1f = take((size_t)o * v * 4);
   L.ovovf = take((size_t)o * v * o * v * 4);
   L.total = off;
@@ -664,12 +679,13 @@ SplitLayout split_layout(int o, int v, int S) {
 
 cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st) {
   const int o = d.o, v = d.v;
-  char *b = (char *)ws;
-  const int blocks = 152 * 8, thr = 256;
-  slice_rows<<<blocks, thr, 0, st>>>(in.ovvv, (long long)o * v * v, v, L.vpad, S, 0, (__nv_bfloat16 *)(b + L.ovvv));
-  slice_rows<<<blocks, thr, 0, st>>>(in.t2, (long long)o * o * v, v, L.vpad, S, 0, (__nv_bfloat16 *)(b + L.t2));
-  slice_t2h<<<blocks, thr, 0, st>>>(in.t2, o, v, L.opad, S, (__nv_bfloat16 *)(b + L.t2h));
-  slice_rows<<<blocks, thr, 0, st>>>(in.ovoo, (long long)o * v * o, o, L.opad, S, 1, (__nv_bfloat16 *)(b + L.ovoo));
+  const int T = (v + NT - 1) / NT, nkb = (v + KC - 1) / KC, nko = (o + KC - 1) / KC;
+  unsigned char *b = (unsigned char *)ws;
+  const int blocks = 152 * 16, thr = 256;
+  build_images<<<blocks, thr, 0, st>>>(0, in.ovvv, o, v, T, nkb, S, b + L.ovvv);
+  build_images<<<blocks, thr, 0, st>>>(1, in.t2, o, v, T, nko, S, b + L.t2h);
+  build_images<<<blocks, thr, 0, st>>>(2, in.t2, o, v, T, nkb, S, b + L.t2);
+  build_images<<<blocks, thr, 0, st>>>(3, in.ovoo, o, v, T, nko, S, b + L.ovoo);
   to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)o * v, (float *)(b + L.t1f));
   to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)o * v * o * v, (float *)(b + L.ovovf));
   return cudaGetLastError();
@@ -679,38 +695,18 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
                          int num_sms, cudaStream_t st) {
   if (S < 2 || S > MAXS) return cudaErrorInvalidValue;
   const int o = d.o, v = d.v;
-  char *b = (char *)ws;
-  CUtensorMap m_ovvv, m_t2, m_t2h, m_ovoo;
-  {  // ovvv slices [S][o][v][v][vpad]: dims (f, b, a, x, slice)
-    const long long dims[5] = {v, v, v, o, S};
-    const long long str[4] = {L.vpad, (long long)v * L.vpad, (long long)v * v * L.vpad, (long long)o * v * v * L.vpad};
-    const int box[5] = {KC, NT, NT, 1, S};   // all S slices in one copy
-    if (!make_map(&m_ovvv, b + L.ovvv, dims, str, box)) return cudaErrorInvalidValue;
-  }
-  {  // t2 slices [S][o][o][v][vpad]: dims (f, c, z, y, slice)
-    const long long dims[5] = {v, v, o, o, S};
-    const long long str[4] = {L.vpad, (long long)v * L.vpad, (long long)o * v * L.vpad, (long long)o * o * v * L.vpad};
-    const int box[5] = {KC, NT, 1, 1, 1};
-    if (!make_map(&m_t2, b + L.t2, dims, str, box)) return cudaErrorInvalidValue;
-  }
-  {  // t2h slices [S][o][v][v][opad]: dims (l, b, a, z, slice)
-    const long long dims[5] = {o, v, v, o, S};
-    const long long str[4] = {L.opad, (long long)v * L.opad, (long long)v * v * L.opad, (long long)o * v * v * L.opad};
-    const int box[5] = {KC, NT, NT, 1, S};   // all S slices in one copy
-    if (!make_map(&m_t2h, b + L.t2h, dims, str, box)) return cudaErrorInvalidValue;
-  }
-  {  // -ovoo slices [S][o][v][o][opad]: dims (l, y, c, x, slice)
-    const long long dims[5] = {o, o, v, o, S};
-    const long long str[4] = {L.opad, (long long)o * L.opad, (long long)v * o * L.opad, (long long)o * v * o * L.opad};
-    const int box[5] = {KC, 1, NT, 1, 1};
-    if (!make_map(&m_ovoo, b + L.ovoo, dims, str, box)) return cudaErrorInvalidValue;
-  }
+  const unsigned char *b = (const unsigned char *)ws;
   SplitParams P{};
   P.d = d;
   P.S = S;
   P.stages = stages_for(S);
   P.kch_p = (v + KC - 1) / KC;
   P.kch_h = (o + KC - 1) / KC;
+  P.T = (v + NT - 1) / NT;
+  P.imgA_p = b + L.ovvv;
+  P.imgA_h = b + L.t2h;
+  P.imgB_p = b + L.t2;
+  P.imgB_h = b + L.ovoo;
   P.t1f = (const float *)(b + L.t1f);
   P.ovovf = (const float *)(b + L.ovovf);
   P.eps = in.eps;
@@ -722,12 +718,11 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
   if (grid > d.n_items) grid = d.n_items;
   if (grid < 1) return cudaSuccess;
   switch (S) {
-    case 2: e = launch_kernel<2>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
-    case 3: e = launch_kernel<3>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
-    default: e = launch_kernel<4>(grid, smem, st, m_ovvv, m_t2, m_t2h, m_ovoo, P); break;
+    case 2: e = launch_kernel<2>(grid, smem, st, P); break;
+    case 3: e = launch_kernel<3>(grid, smem, st, P); break;
+    default: e = launch_kernel<4>(grid, smem, st, P); break;
   }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace tc
