@@ -107,3 +107,21 @@ def test_invalid_slice_counts():
         with pytest.raises(tc.TcError) as ei:
             gpu_util.energy_host(job, prec=SPLIT, slices=s)
         assert ei.value.status == tc.TC_EINVAL
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(__import__("os").path.join(
+    __import__("os").path.dirname(__import__("os").path.abspath(__file__)), "golden", "single_o20_v200.json")),
+    reason="golden not generated")
+@pytest.mark.parametrize("s", [2, 3])
+def test_single_o20_v200_against_stored_oracle(s):
+    """The o=20, v=200 workload: E_T and every triplet contribution vs the stored oracle values."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "single_o20_v200.json")))
+    job = synth.workload_job("single_o20_v200")
+    r, e_ijk = gpu_util.energy_dev(job, prec=SPLIT, slices=s, want_trip=True)
+    print(f"s={s} E={r.e_t:.10e} ref={gold['e_t']:.10e} rel={abs(r.e_t - gold['e_t']) / abs(gold['e_t']):.2e}")
+    assert abs(r.e_t - gold["e_t"]) <= rel_bound(s, gold["e_t"])
+    scale = max(abs(t[3]) for t in gold["triplets"])
+    for i, j, k, x in gold["triplets"]:
+        assert abs(e_ijk[i, j, k] - x) <= 10 * REL[s] * scale
