@@ -2,17 +2,24 @@
 """Benchmark of the (T) correction: (T) TFLOP/s and seconds per energy.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--prec fp64|split] [--slices S]
+                    [--workload NAME] [--prec both|split|fp64] [--slices S]
 
-A step is one full (T) energy (every hot-path stage: work tables, fused
-W/V/energy kernel, compensated reduction, read-back of E_T) on one seeded
-synthetic job whose inputs are resident in HBM before timing starts.  The
-inputs (ovvv alone is >1 GB at o=20, v=200) exceed the 129 MB L2, so no L2
-flush is needed between steps.  With N > 1 (torchrun) every rank solves its
-own copy of the job (independent problems, no collective on the data path):
-weak scaling, value = total energies' FLOPs / max-over-ranks time.
+A step is one full (T) energy -- every hot-path stage: BF16 slicing into
+tensor-core images (split path), work tables, the fused W/V/energy kernel,
+compensated reduction and the read-back of E_T -- on one seeded synthetic job
+whose inputs are resident in HBM before timing starts.  The inputs (ovvv
+alone is 1.28 GB at o=20, v=200) exceed the 129 MB L2, so no L2 flush is
+needed between steps.
 
---impl reference times the CPU oracle (tests' ground truth) on a bounded
+Headline ("value"): the split-precision path (BF16 slices, s = --slices) on
+the o=20, v=200 workload; beside it ("fp64") the FP64 tensor-core path on the
+same job (fewer steps: one energy takes ~30 s) and |dE| between the two.
+
+With N > 1 (torchrun) every rank solves its own copy of the job (independent
+problems, no collective on the data path): weak scaling, value = total
+energies' FLOPs / max-over-ranks time.
+
+--impl reference times the CPU oracle (the tests' ground truth) on a bounded
 sample of occupied triplets of the same workload, on this host's cores.
 """
 from __future__ import annotations
@@ -48,7 +55,8 @@ def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         m = json.load(open(p))
-        return m.get("bf16_tflops", FALLBACK_BF16_TF), m.get("bf16_tflops_sustained"), m.get("hbm_gbs", FALLBACK_HBM), "measured"
+        return (m.get("bf16_tflops", FALLBACK_BF16_TF), m.get("bf16_tflops_sustained"),
+                m.get("hbm_gbs", FALLBACK_HBM), "measured")
     return FALLBACK_BF16_TF, None, FALLBACK_HBM, "fallback"
 
 
@@ -135,15 +143,35 @@ def cores():
         return os.cpu_count()
 
 
+def reference_arm(args, name, o, v, flops, metric):
+    job = synth.workload_job(name)
+    vals = []
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    info = ""
+    for s in range(args.warmup + args.steps):
+        proj, info = oracle_sample(job, per_step, seed=4242 + s)
+        if s >= args.warmup:
+            vals.append(flops / proj / 1e12)
+    val = statistics.median(vals)
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * flops / (val * 1e12),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "o": o, "v": v, "prec": "fp64", "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle", "sample": info},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="single_o20_v200", choices=sorted(synth.WORKLOADS))
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--prec", default="both", choices=["both", "split", "fp64"])
     ap.add_argument("--slices", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -157,23 +185,8 @@ def main():
     metric = "(T) TFLOP/s"
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        job = synth.workload_job(name)
-        vals = []
-        per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-        for s in range(args.warmup + args.steps):
-            proj, info = oracle_sample(job, per_step, seed=4242 + s)
-            if s >= args.warmup:
-                vals.append(flops / proj / 1e12)
-        val = statistics.median(vals)
-        print(json.dumps({
-            "impl": "reference", "metric": metric, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * flops / (val * 1e12),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "o": o, "v": v, "prec": "fp64", "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle", "sample": info},
-            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        if rank == 0:
+            reference_arm(args, name, o, v, flops, metric)
         return
 
     import torch
@@ -193,45 +206,57 @@ def main():
         tcbuild.build()
     dev_id = torch.cuda.current_device()
 
-    prec = tc.TC_FP64 if args.prec == "fp64" else tc.TC_SPLIT_BF16
-    slices = 0 if prec == tc.TC_FP64 else args.slices
+    head_prec = tc.TC_FP64 if args.prec == "fp64" else tc.TC_SPLIT_BF16
+    head_slices = 0 if head_prec == tc.TC_FP64 else args.slices
     job = synth.workload_job(name)
     names = ("eps", "t1", "t2", "ovvv", "ovoo", "ovov")
     dev = {k: torch.from_numpy(getattr(job, k)).to(f"cuda:{dev_id}") for k in names}
     ctx = tc.tc_init(dev_id)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(prec, slices):
         return tc.tc_energy_dev(ctx, o, v, dev["eps"], dev["t1"], dev["t2"], dev["ovvv"], dev["ovoo"], dev["ovov"],
                                 prec=prec, slices=slices, stream=stream)
 
-    for _ in range(args.warmup):
-        r = step()
-    e_ref = r.e_t
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern, launches = [], 0
-    with ClockSampler(dev_id) as clk:
+    def timed(prec, slices, warmup, steps, sample_clocks):
+        r = None
+        for _ in range(warmup):
+            r = step(prec, slices)
+        e_ref = r.e_t if r is not None else None
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kern, prep, launches = [], [], 0
+        clk = ClockSampler(dev_id) if sample_clocks else None
+        if clk:
+            clk.__enter__()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
-            r = step()
+        for _ in range(steps):
+            r = step(prec, slices)
             kern.append(r.kernel_seconds)
+            prep.append(r.prep_seconds)
             launches += r.launches
-            assert r.e_t == e_ref, "energy changed between steps"
+            assert e_ref is None or r.e_t == e_ref, "energy changed between steps"
+            e_ref = r.e_t
         ev1.record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    clocks = clk.summary()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        tt = torch.tensor([t], device=f"cuda:{dev_id}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    sec = t / args.steps
-    value = world * flops / sec / 1e12
+        if clk:
+            clk.__exit__()
+        t = ev0.elapsed_time(ev1) / 1e3
+        if dist:
+            tt = torch.tensor([t], device=f"cuda:{dev_id}", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return {"sec": t / steps, "e_t": e_ref, "kernel": statistics.mean(kern), "prep": statistics.mean(prep),
+                "launches": launches, "clocks": clk.summary() if clk else None}
+
+    head = timed(head_prec, head_slices, args.warmup, args.steps, True)
+    fp64 = None
+    if args.prec == "both":
+        fp64 = timed(tc.TC_FP64, 0, 1, args.fp64_steps, False)
 
     # end to end through the host entry point: pinned host inputs -> E_T on the host
     host = {}
@@ -240,16 +265,19 @@ def main():
         pt.numpy()[...] = getattr(job, k)
         host[k] = pt.numpy()
     h2d = sum(host[k].nbytes for k in names)
-    tc.tc_energy(ctx, o, v, host["eps"], host["t1"], host["t2"], host["ovvv"], host["ovoo"], host["ovov"],
-                 prec=prec, slices=slices)
+
+    def host_step():
+        return tc.tc_energy(ctx, o, v, host["eps"], host["t1"], host["t2"], host["ovvv"], host["ovoo"], host["ovov"],
+                            prec=head_prec, slices=head_slices)
+
+    host_step()
     if dist:
         dist.barrier()
+    e2e_steps = max(1, args.steps)
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 2))
     for _ in range(e2e_steps):
-        re = tc.tc_energy(ctx, o, v, host["eps"], host["t1"], host["t2"], host["ovvv"], host["ovoo"],
-                          host["ovov"], prec=prec, slices=slices)
-        assert re.e_t == e_ref
+        re = host_step()
+        assert re.e_t == head["e_t"]
     te = (time.perf_counter() - t0) / e2e_steps
     if dist:
         tt = torch.tensor([te], device=f"cuda:{dev_id}", dtype=torch.float64)
@@ -257,37 +285,44 @@ def main():
         te = float(tt.item())
 
     bf16_peak, bf16_sus, hbm, src = peaks()
-    ksec = statistics.mean(kern)
-    if prec == tc.TC_FP64:
-        kname = "tc_fp64_kernel"
+    if head_prec == tc.TC_FP64:
+        kname, pairs = "tc_fp64_kernel", 1
         peak = bf16_peak * FP64_NOMINAL_TF / BF16_NOMINAL_TF
-        achieved = flops / ksec / 1e12
-        bound = "tensor"
-        peak_note = f"FP64 tensor (DMMA) peak = {src} bf16 burst x nominal FP64/BF16 ratio (1.25/2250)"
+        peak_note = f"FP64 tensor (DMMA) peak = {src} bf16 burst x nominal FP64/BF16 ratio 1.25/2250"
     else:
-        kname = "tc_split_kernel"
-        peak = bf16_sus or bf16_peak
-        achieved = flops * (slices * (slices + 1) / 2) / ksec / 1e12
-        bound = "tensor"
-        peak_note = f"BF16 {src} peak; achieved counts executed slice-pair flops"
-    out = None
+        kname, pairs = "tc_split_kernel", head_slices * (head_slices + 1) // 2
+        peak = bf16_peak
+        peak_note = (f"BF16 dense {src} burst peak; achieved counts the s(s+1)/2 = {pairs} slice-pair products "
+                     f"of 2(o^3 v^4 + o^4 v^3) flop")
+    achieved = flops * pairs / head["kernel"] / 1e12
     if rank == 0:
         out = {
-            "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == tc.TC_FP64 else "bf16x%d->f32->f64" % slices,
+            "metric": metric, "value": world * flops / head["sec"] / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * head["sec"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head_prec == tc.TC_FP64 else f"bf16x{head_slices}->f32, f64 denominator+sums",
             "data": "synthetic (seeded DF integrals and amplitudes)",
-            "config": {"workload": name, "o": o, "v": v, "prec": args.prec, "slices": slices,
-                       "s_per_energy": sec, "e_t": e_ref, "l2": "inputs larger than L2 (ovvv %.2f GB)"
-                       % (job.ovvv.nbytes / 1e9)},
-            "clocks": clocks,
+            "config": {"workload": name, "o": o, "v": v, "prec": args.prec, "slices": head_slices,
+                       "s_per_energy": head["sec"], "e_t": head["e_t"], "prep_ms": 1e3 * head["prep"],
+                       "l2": "inputs larger than L2 (ovvv %.2f GB)" % (job.ovvv.nbytes / 1e9)},
+            "clocks": head["clocks"],
             "e2e": {"value": world * flops / te / 1e12, "unit": "TFLOP/s", "s_per_energy": te,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-            "gpu_launches": launches,
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(kname, name, args.prec),
-                         "kernel": kname, "kernel_ms": 1e3 * ksec, "peak_source": peak_note},
+            "gpu_launches": head["launches"],
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(kname, name, "fp64" if pairs == 1 else "split"),
+                         "kernel": kname, "kernel_ms": 1e3 * head["kernel"], "peak_source": peak_note},
         }
+        if fp64 is not None:
+            fpeak = bf16_peak * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+            fach = flops / fp64["kernel"] / 1e12
+            out["fp64"] = {"value": world * flops / fp64["sec"] / 1e12, "unit": "TFLOP/s", "s_per_energy": fp64["sec"],
+                           "steps": args.fp64_steps, "warmup": 1, "e_t": fp64["e_t"],
+                           "roofline": {"bound": "tensor", "achieved": fach, "peak": fpeak, "frac": fach / fpeak,
+                                        "kernel": "tc_fp64_kernel"}}
+            out["config"]["abs_dE_split_vs_fp64"] = abs(head["e_t"] - fp64["e_t"])
+            out["config"]["rel_dE_split_vs_fp64"] = abs(head["e_t"] - fp64["e_t"]) / abs(fp64["e_t"])
+            out["config"]["speedup_split_vs_fp64"] = fp64["sec"] / head["sec"]
         if world == 1 and not args.no_cpu_baseline:
             proj, info = oracle_sample(job, args.cpu_baseline_seconds)
             out["cpu_baseline"] = {"value": flops / proj / 1e12, "unit": "TFLOP/s", "cores": cores(),
