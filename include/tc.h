@@ -114,6 +114,21 @@ tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const doub
                         const double *t2, const tc_ints *ints, int prec, int slices,
                         double *e_ijk_dev, void *stream, tc_result *out);
 
+/* Weighted contributions of selected occupied triplets (the i >= j >= k
+ * regrouping of Eq. 1: E_(T) is the sum over all triplets).  Same inputs as
+ * tc_energy_dev (DEVICE pointers, read in place).
+ *   trip   HOST array [n][3] of (i, j, k) with o > i >= j >= k >= 0, any order,
+ *          repeats allowed.
+ *   e_out  HOST array [n]: e_out[m] receives the contribution of trip[m]
+ *          (0 when i == j == k).
+ * Uses: checking sampled triplets of a large job against a reference,
+ * splitting one energy across devices or calls, resuming by triplet range.
+ * out->e_t is the sum of e_out.  TC_EINVAL on an out-of-range or unordered
+ * triplet (nothing is launched). */
+tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
+                          const double *t2, const tc_ints *ints, int prec, int slices,
+                          const int *trip, int n, double *e_out, void *stream, tc_result *out);
+
 /* Size of the library's static device scratch array used by
  * tc_energy_dev_noalloc (held on every GPU that loads the library). */
 #define TC_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)

@@ -18,7 +18,7 @@ TC_FP64, TC_SPLIT_BF16 = 0, 1
 
 #: Every symbol include/tc.h declares (the CPU test checks the library exports them).
 EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
-           "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc")
+           "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc", "tc_triplets_dev")
 
 #: TC_NOALLOC_SCRATCH_BYTES of include/tc.h
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -79,6 +79,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_energy_dev_noalloc.argtypes = [i, i, vp, vp, vp, ctypes.POINTER(tc_ints), vp, vp, vp,
                                           ctypes.c_char_p, sz]
     lib.tc_energy_dev_noalloc.restype = i
+    lib.tc_triplets_dev.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(tc_ints), i, i, vp, i, vp, vp,
+                                    ctypes.POINTER(tc_result)]
+    lib.tc_triplets_dev.restype = i
     del d, dp
     _lib = lib
     return lib
@@ -160,6 +163,24 @@ def tc_energy_dev(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices
                              slices, _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(res))
     _check(ctx, s)
     return res
+
+
+def tc_triplets_dev(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, triplets, prec=TC_FP64, slices=0,
+                    stream=None):
+    """Weighted contributions of the listed (i, j, k), i >= j >= k; returns (numpy array [n], tc_result)."""
+    import numpy as np
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    trip = np.ascontiguousarray(np.asarray(triplets, dtype=np.int32).reshape(-1, 3))
+    e_out = np.zeros(trip.shape[0], dtype=np.float64)
+    ints = tc_ints(_ptr_dev(ovvv), _ptr_dev(ovoo), _ptr_dev(ovov))
+    res = tc_result()
+    s = load().tc_triplets_dev(ctx, o, v, _ptr_dev(eps), _ptr_dev(t1), _ptr_dev(t2), ctypes.byref(ints), prec, slices,
+                               trip.ctypes.data, trip.shape[0], e_out.ctypes.data,
+                               ctypes.c_void_p(stream.cuda_stream), ctypes.byref(res))
+    _check(ctx, s)
+    return e_out, res
 
 
 def tc_energy_dev_noalloc(o, v, eps, t1, t2, ovvv, ovoo, ovov, e_t, e_ijk=None, stream=None) -> None:

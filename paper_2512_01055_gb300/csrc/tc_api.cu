@@ -74,14 +74,14 @@ tc_status fail(tc_ctx *ctx, tc_status s, const char *fmt, ...) {
                   __FILE__, __LINE__);                                                      \
   } while (0)
 
-tc::Dims make_dims(int o, int v, int nt) {
+tc::Dims make_dims(int o, int v, int nt, int n_trip_override = -1) {
   tc::Dims d{};
   d.o = o;
   d.v = v;
   d.nt = nt;
   d.ntiles = (v + nt - 1) / nt;
   const long long T = d.ntiles;
-  d.n_trip = (int)((long long)o * (o + 1) * (o + 2) / 6 - o);
+  d.n_trip = n_trip_override >= 0 ? n_trip_override : (int)((long long)o * (o + 1) * (o + 2) / 6 - o);
   d.n_orb = (int)(T * (T + 1) * (T + 2) / 6);
   const long long pairs = (long long)d.n_trip * d.n_orb;
   const long long target = 4LL << 20;   // at most ~4M partials
@@ -106,18 +106,25 @@ size_t table_bytes(const tc::Dims &d) {
   return align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) + sizeof(int4) * (size_t)std::max(1, d.n_orb);
 }
 
-tc_status ensure_tables(tc_ctx *ctx, const tc::Dims &d, cudaStream_t st, const int4 **trip, const int4 **orb) {
+// Triplet and orbit tables.  subset (optional): the triplets to process
+// instead of all of them (already checked, all-equal triplets removed).
+tc_status ensure_tables(tc_ctx *ctx, const tc::Dims &d, cudaStream_t st, const int4 **trip, const int4 **orb,
+                        const std::vector<int4> *subset) {
   const size_t tb = table_bytes(d);
-  if (!(ctx->tab_o == d.o && ctx->tab_v == d.v && ctx->tab_nt == d.nt && ctx->tables.cap >= tb)) {
+  if (subset || !(ctx->tab_o == d.o && ctx->tab_v == d.v && ctx->tab_nt == d.nt && ctx->tables.cap >= tb)) {
     std::vector<int4> h(tb / sizeof(int4) + 1);
     int4 *ht = h.data();
     int n = 0;
-    for (int i = 0; i < d.o; ++i)
-      for (int j = 0; j <= i; ++j)
-        for (int k = 0; k <= j; ++k) {
-          if (i == k) continue;                       // i == j == k: zero contribution
-          ht[n++] = make_int4(i, j, k, 2 - (i == j) - (j == k));
-        }
+    if (subset) {
+      for (const int4 &t : *subset) ht[n++] = t;
+    } else {
+      for (int i = 0; i < d.o; ++i)
+        for (int j = 0; j <= i; ++j)
+          for (int k = 0; k <= j; ++k) {
+            if (i == k) continue;                     // i == j == k: zero contribution
+            ht[n++] = make_int4(i, j, k, 2 - (i == j) - (j == k));
+          }
+    }
     int4 *ho = ht + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) / sizeof(int4);
     int m = 0;
     for (int P = 0; P < d.ntiles; ++P)
@@ -127,7 +134,8 @@ tc_status ensure_tables(tc_ctx *ctx, const tc::Dims &d, cudaStream_t st, const i
     TC_CUDA(ctx, ctx->tables.ensure(tb));
     TC_CUDA(ctx, cudaMemcpyAsync(ctx->tables.p, ht, tb, cudaMemcpyHostToDevice, st));
     TC_CUDA(ctx, cudaStreamSynchronize(st));
-    ctx->tab_o = d.o; ctx->tab_v = d.v; ctx->tab_nt = d.nt;
+    if (subset) { ctx->tab_o = -1; ctx->tab_v = -1; ctx->tab_nt = -1; }   // not the full table
+    else { ctx->tab_o = d.o; ctx->tab_v = d.v; ctx->tab_nt = d.nt; }
   }
   *trip = (const int4 *)ctx->tables.p;
   *orb = (const int4 *)((char *)ctx->tables.p + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)));
@@ -160,16 +168,17 @@ double alg_flops(int o, int v) {
 
 // The hot path on device-resident inputs.  Caller holds ctx->mu.
 tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, int slices, double *e_ijk_dev,
-                     cudaStream_t st, tc_result *out) {
+                     cudaStream_t st, tc_result *out, const std::vector<int4> *subset = nullptr,
+                     std::vector<double> *e_sub = nullptr) {
   const bool split = (prec == TC_SPLIT_BF16);
   const int nt = split ? tc::split_tile() : tc::fp64_tile();
-  const tc::Dims d = make_dims(o, v, nt);
+  const tc::Dims d = make_dims(o, v, nt, subset ? (int)subset->size() : -1);
   const Layout L = make_layout(d);
   const tc::SplitLayout SL = split ? tc::split_layout(o, v, slices) : tc::SplitLayout{};
   const size_t need = L.total + table_bytes(d) + SL.total;
   if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "workspace %zu B exceeds budget %zu B", need, ctx->budget);
   const int4 *trip = nullptr, *orb = nullptr;
-  tc_status s = ensure_tables(ctx, d, st, &trip, &orb);
+  tc_status s = ensure_tables(ctx, d, st, &trip, &orb, subset);
   if (s != TC_OK) return s;
   TC_CUDA(ctx, ctx->ws.ensure(L.total));
   if (split) TC_CUDA(ctx, ctx->ws_split.ensure(SL.total));
@@ -216,6 +225,13 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
     return fail(ctx, (errflag >= 11 && errflag <= 15) ? TC_ETIMEOUT : TC_EINTERNAL,
                 "device-side wait gave up (code %d)", errflag);
   out->e_t = ctx->host_out[0];
+  if (e_sub) {
+    e_sub->assign((size_t)d.n_trip, 0.0);
+    if (d.n_trip > 0) {
+      TC_CUDA(ctx, cudaMemcpyAsync(e_sub->data(), e_trip, sizeof(double) * (size_t)d.n_trip, cudaMemcpyDeviceToHost, st));
+      TC_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+  }
   if (d.n_items > 0) {
     float ms = 0.f;
     TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
@@ -331,6 +347,38 @@ tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const doub
   if (s != TC_OK) return s;
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out->tflops_alg = alg_flops(o, v) / std::max(out->seconds, 1e-12) / 1e12;
+  return TC_OK;
+}
+
+tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
+                          const tc_ints *ints, int prec, int slices, const int *trip, int n, double *e_out,
+                          void *stream, tc_result *out) {
+  if (!ctx || !out) return TC_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  tc_status s = check_args(ctx, o, v, eps, t1, t2, ints, &prec, &slices);
+  if (s != TC_OK) return s;
+  if (n < 0 || (n > 0 && (!trip || !e_out))) return fail(ctx, TC_EINVAL, "bad triplet list");
+  std::vector<int4> sub;
+  std::vector<int> where;                  // position in the caller's list of each processed triplet
+  for (int m = 0; m < n; ++m) {
+    const int i = trip[3 * m], j = trip[3 * m + 1], k = trip[3 * m + 2];
+    if (!(o > i && i >= j && j >= k && k >= 0))
+      return fail(ctx, TC_EINVAL, "triplet %d = (%d, %d, %d) is not o > i >= j >= k >= 0", m, i, j, k);
+    e_out[m] = 0.0;
+    if (i == k) continue;
+    sub.push_back(make_int4(i, j, k, 2 - (i == j) - (j == k)));
+    where.push_back(m);
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  TC_CUDA(ctx, cudaSetDevice(ctx->device));
+  tc::Inputs in{eps, t1, t2, ints->ovvv, ints->ovoo, ints->ovov};
+  std::memset(out, 0, sizeof *out);
+  std::vector<double> e_sub;
+  s = run_device(ctx, o, v, in, prec, slices, nullptr, (cudaStream_t)stream, out, &sub, &e_sub);
+  if (s != TC_OK) return s;
+  for (size_t q = 0; q < where.size(); ++q) e_out[where[q]] = e_sub[q];
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return TC_OK;
 }
 

@@ -233,3 +233,28 @@ def serving_request_shape(r: int) -> tuple[int, int]:
     o = 6 + int(u[0] * 27)
     v = int(round(o * (6.0 + 6.0 * u[1])))
     return o, v
+
+
+# ---------------------------------------------------------------------------
+# Device copies of a job (large workloads): the integral blocks are formed on
+# the GPU with FP64 matrix products of the same DF factor.  Because every B
+# value sits on a 2^-20 grid, each product sum is exact, so the device blocks
+# are bit-identical to the host ones (tests check this on sampled slices).
+# ---------------------------------------------------------------------------
+
+def device_job(amp: Amplitudes, device="cuda"):
+    """dict of device float64 tensors eps, t1, t2, ovvv, ovoo, ovov for one job."""
+    import torch
+    o, v, Q = amp.o, amp.v, amp.Q
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    Bov = f(amp.B[:, :o, o:]).reshape(Q, o * v)
+    Bvv = f(amp.B[:, o:, o:]).reshape(Q, v * v)
+    Boo = f(amp.B[:, :o, :o]).reshape(Q, o * o)
+    ovvv = torch.empty((o, v, v, v), dtype=torch.float64, device=device)
+    for i in range(o):
+        ovvv[i] = (Bov.reshape(Q, o, v)[:, i, :].T @ Bvv).reshape(v, v, v)
+    out = dict(eps=f(amp.eps), t1=f(amp.t1), t2=f(amp.t2), ovvv=ovvv,
+               ovoo=(Bov.T @ Boo).reshape(o, v, o, o).contiguous(),
+               ovov=(Bov.T @ Bov).reshape(o, v, o, v).contiguous())
+    del Bov, Bvv, Boo
+    return out
