@@ -193,7 +193,7 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   double *dout = (double *)(base + L.out);
   TC_CUDA(ctx, cudaMemsetAsync(w.counter, 0, 2 * sizeof(unsigned), st));
   if (e_ijk_dev) TC_CUDA(ctx, cudaMemsetAsync(e_ijk_dev, 0, sizeof(double) * (size_t)o * o * o, st));
-  int launches = 1;                                      // reduce_total
+  int launches = 1;                                      // reduce_jobs
   if (split) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
     TC_CUDA(ctx, tc::launch_split_prep(d, slices, in, ctx->ws_split.p, SL, st));
@@ -203,19 +203,32 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   if (d.n_items > 0) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     if (split) {
-      TC_CUDA(ctx, tc::launch_split(d, slices, in, ctx->ws_split.p, SL, w, ctx->num_sms, st));
+      tc::SplitBatch b{};
+      b.njobs = 1;
+      b.err = w.err;
+      b.job[0] = tc::split_job(d, in, ctx->ws_split.p, SL, w);
+      TC_CUDA(ctx, tc::launch_split(b, slices, ctx->num_sms, st));
     } else {
       int per_sm = 0;
       TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
       long long grid = (long long)ctx->num_sms * per_sm;
       grid = std::min<long long>(grid, d.n_items);
-      TC_CUDA(ctx, tc::launch_fp64(d, in, w, (int)grid, st));
+      tc::FpBatch b{};
+      b.njobs = 1;
+      b.total_items = d.n_items;
+      b.counter = w.counter;
+      b.job[0] = tc::FpJob{d, in, w, 0};
+      TC_CUDA(ctx, tc::launch_fp64(b, (int)grid, st));
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     launches += 1;
   }
-  if (d.n_trip > 0) launches += 1;                       // reduce_triplets
-  TC_CUDA(ctx, tc::launch_reduce(d, w, e_trip, e_ijk_dev, dout, st));
+  {
+    tc::RedBatch rb{};
+    rb.njobs = 1;
+    rb.job[0] = tc::RedJob{d.n_trip, d.items_per_trip, o, w.trip, w.partial, e_trip, e_ijk_dev, dout};
+    TC_CUDA(ctx, tc::launch_reduce(rb, st));
+  }
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out + 2, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TC_CUDA(ctx, cudaStreamSynchronize(st));

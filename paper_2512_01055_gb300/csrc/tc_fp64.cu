@@ -41,7 +41,7 @@ __device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
 }
 
 __global__ void __launch_bounds__(THREADS, 2)
-tc_fp64_kernel(Dims d, Inputs in, Work w) {
+tc_fp64_kernel(const __grid_constant__ FpBatch B) {
   extern __shared__ double smem[];
   double *Ws = smem;                     // [6][NT3]   W of the orbit's blocks
   double *As = Ws + 6 * NT3;             // [6][NT2][LDA] particle A rows, one set per u
@@ -50,14 +50,19 @@ tc_fp64_kernel(Dims d, Inputs in, Work w) {
   __shared__ double s_red[THREADS / 32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int o = d.o, v = d.v;
-  const long long vv = (long long)v * v;
-
   for (;;) {
-    if (tid == 0) s_item = (long long)atomicAdd(w.counter, 1u);
+    if (tid == 0) s_item = (long long)atomicAdd(B.counter, 1u);
     __syncthreads();
-    const long long item = s_item;
-    if (item >= d.n_items) break;
+    const long long gitem = s_item;
+    if (gitem >= B.total_items) break;
+    int jc = 0;                                  // the job owning this global item
+    while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;
+    const Dims &d = B.job[jc].d;
+    const Inputs &in = B.job[jc].in;
+    const Work &w = B.job[jc].w;
+    const long long item = gitem - B.job[jc].item0;
+    const int o = d.o, v = d.v;
+    const long long vv = (long long)v * v;
     const int t = (int)(item / d.items_per_trip);
     const int chunk = (int)(item % d.items_per_trip);
     const int4 tr = w.trip[t];
@@ -229,10 +234,10 @@ cudaError_t fp64_blocks_per_sm(int *n) {
   return e;
 }
 
-cudaError_t launch_fp64(const Dims &d, const Inputs &in, const Work &w, int grid, cudaStream_t st) {
+cudaError_t launch_fp64(const FpBatch &b, int grid, cudaStream_t st) {
   cudaError_t e = configure();
   if (e != cudaSuccess) return e;
-  tc_fp64_kernel<<<grid, THREADS, fp64_smem_bytes(), st>>>(d, in, w);
+  tc_fp64_kernel<<<grid, THREADS, fp64_smem_bytes(), st>>>(b);
   return cudaGetLastError();
 }
 

@@ -11,17 +11,24 @@
 //     everything the energy bracket of Eq. 1 needs;
 //   * a work item is (triplet, chunk of consecutive orbits); each item writes
 //     one FP64 partial, so the result does not depend on which CTA ran it.
+//
+// Every kernel takes a batch of up to MAX_BATCH independent jobs by value;
+// the global item range is the concatenation of the jobs' item ranges.  A
+// job's result depends only on its own items, so it is the same alone or in
+// any batch.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace tc {
 
+constexpr int MAX_BATCH = 32;
+
 struct Dims {
   int o, v;
   int nt;              // tile edge
   int ntiles;          // ceil(v / nt)
-  int n_trip;          // triplets i >= j >= k without i == j == k
+  int n_trip;          // triplets processed (all i >= j >= k without i == j == k, or a subset)
   int n_orb;           // tile triples P >= Q >= R
   int orb_per_item;
   int items_per_trip;
@@ -52,25 +59,68 @@ __host__ __device__ constexpr int perm3(int s, int pos) {
 }
 __host__ __device__ constexpr bool perm3_even(int s) { return s == 0 || s == 3 || s == 4; }
 
-// Host-side launchers (defined in the .cu files).
-cudaError_t launch_fp64(const Dims &d, const Inputs &in, const Work &w, int grid, cudaStream_t st);
+// ---------------------------------------------------------------- FP64 path
+struct FpJob {
+  Dims d;
+  Inputs in;
+  Work w;
+  long long item0;     // first global item of this job
+};
+struct FpBatch {
+  int njobs;
+  long long total_items;
+  unsigned int *counter;   // global work counter of the launch (zeroed before it)
+  FpJob job[MAX_BATCH];
+};
 int fp64_tile();
 size_t fp64_smem_bytes();
 cudaError_t fp64_blocks_per_sm(int *n);
-cudaError_t launch_reduce(const Dims &d, const Work &w, double *e_trip, double *e_ijk, double *out,
-                          cudaStream_t st);
+cudaError_t launch_fp64(const FpBatch &b, int grid, cudaStream_t st);
 
-// Split-precision path (tc_split.cu): byte offsets of the BF16 slices and FP32
-// copies inside its workspace.
+// ---------------------------------------------------------------- split path
+// Byte offsets of the BF16 operand images and FP32 copies inside a job's
+// split workspace.
 struct SplitLayout {
-  int vpad, opad;                          // row pitches (elements), multiples of 8
-  size_t ovvv, t2, t2h, ovoo, t1f, ovovf;  // offsets
+  int vpad, opad;
+  size_t ovvv, t2, t2h, ovoo, t1f, ovovf;
   size_t total;
+};
+struct SplitJob {
+  Dims d;
+  int kch_p, kch_h;      // K blocks (of 16) of particle / hole products
+  int T;                 // virtual tiles
+  const unsigned char *imgA_p, *imgA_h, *imgB_p, *imgB_h;   // operand images
+  const float *t1f, *ovovf;
+  const double *eps;
+  Work w;
+  long long item0;
+};
+struct SplitBatch {
+  int njobs;
+  int stages;            // set by launch_split
+  long long total_items;
+  int *err;
+  SplitJob job[MAX_BATCH];
 };
 int split_tile();
 SplitLayout split_layout(int o, int v, int S);
 cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st);
-cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, const Work &w,
-                         int num_sms, cudaStream_t st);
+SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitLayout &L, const Work &w);
+cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st);
+
+// ---------------------------------------------------------------- reduction
+struct RedJob {
+  int n_trip, items_per_trip, o;
+  const int4 *trip;
+  const double *partial;
+  double *e_trip;        // [n_trip] weighted triplet contributions
+  double *e_ijk;         // optional [o][o][o]
+  double *out;           // [2]: E and sum |e|
+};
+struct RedBatch {
+  int njobs;
+  RedJob job[MAX_BATCH];
+};
+cudaError_t launch_reduce(const RedBatch &b, cudaStream_t st);
 
 }  // namespace tc

@@ -183,9 +183,19 @@ extern "C" tc_status tc_energy_dev_noalloc(int o, int v, const double *eps, cons
   if (d.n_items > 0) {
     long long grid = (long long)su.num_sms * su.blocks_per_sm;
     if (grid > d.n_items) grid = d.n_items;
-    NA_CUDA(tc::launch_fp64(d, in, w, (int)grid, st));
+    tc::FpBatch b{};
+    b.njobs = 1;
+    b.total_items = d.n_items;
+    b.counter = w.counter;
+    b.job[0] = tc::FpJob{d, in, w, 0};
+    NA_CUDA(tc::launch_fp64(b, (int)grid, st));
   }
-  NA_CUDA(tc::launch_reduce(d, w, e_trip, e_ijk_dev, out, st));
+  {
+    tc::RedBatch rb{};
+    rb.njobs = 1;
+    rb.job[0] = tc::RedJob{d.n_trip, d.items_per_trip, o, w.trip, w.partial, e_trip, e_ijk_dev, out};
+    NA_CUDA(tc::launch_reduce(rb, st));
+  }
   NA_CUDA(cudaMemcpyAsync(e_t_dev, out, sizeof(double), cudaMemcpyDeviceToDevice, st));
 #undef NA_CUDA
   return TC_OK;

@@ -91,17 +91,6 @@ __host__ __device__ __forceinline__ int pattern_id(const int occ[3], const int t
   return op * 4 + tp;
 }
 
-struct SplitParams {
-  Dims d;
-  int S;
-  int stages;
-  int kch_p, kch_h;      // K blocks (of 16) of particle / hole jobs
-  int T;                 // virtual tiles
-  const unsigned char *imgA_p, *imgA_h, *imgB_p, *imgB_h;   // operand images
-  const float *t1f, *ovovf;
-  const double *eps;
-  Work w;
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -248,11 +237,11 @@ int host_build_template(const int occ[3], const int tl[3], TJob *jobs) {
 
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-tc_split_kernel(const SplitParams P) {
+tc_split_kernel(const __grid_constant__ SplitBatch B) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
-  float *Wsm = (float *)(sm + P.stages * STAGE_BYTES);
+  float *Wsm = (float *)(sm + B.stages * STAGE_BYTES);
 
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar;
@@ -262,11 +251,9 @@ tc_split_kernel(const SplitParams P) {
   __shared__ double red[EPI_WARPS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Dims &d = P.d;
-  const int o = d.o, v = d.v;
 
   if (tid == 0) {
-    for (int s = 0; s < P.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    for (int s = 0; s < B.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(&accfull_bar[b], 1); mbar_init(&accempty_bar[b], 1); }
     mbar_init(&teardown_bar, 1);
     abort_flag = 0;
@@ -290,7 +277,14 @@ tc_split_kernel(const SplitParams P) {
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+    int jc = 0;
+    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
+      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
+      const SplitJob &P = B.job[jc];
+      const Dims &d = P.d;
+      const int o = d.o, v = d.v;
+      const long long item = gitem - P.item0;
+      (void)v;
       const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
       const int4 tr = P.w.trip[t];
       const int occ[3] = {tr.x, tr.y, tr.z};
@@ -321,7 +315,7 @@ tc_split_kernel(const SplitParams P) {
           for (int kc = 0; kc < nk; ++kc) {
             int got = 1;
             if (lane == 0) {
-              got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
+              got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
               if (got) mbar_expect_tx(&full_bar[stage], bytes);
             }
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -335,20 +329,20 @@ tc_split_kernel(const SplitParams P) {
                         &full_bar[stage]);
             }
             __syncwarp();
-            if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+            if (++stage == B.stages) { stage = 0; phase ^= 1u; }
           }
         }
       }
     }
     // wait for every copy this warp issued (bounded) before the CTA may exit
     if (lane == 0) {
-      for (int s = 0; s < P.stages; ++s) {
+      for (int s = 0; s < B.stages; ++s) {
         // the most recent use of stage s had parity phase if s < stage, else phase ^ 1
         const uint32_t par = (s >= stage) ? (phase ^ 1u) : phase;
         const uint32_t a = smem_u32(&full_bar[s]);
         for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, par); ++it) {
           if ((it & 255) == 255) __nanosleep(128);
-          if (it == WAIT_LIMIT - 1) atomicCAS(P.w.err, 0, ERR_TIMEOUT_TEARDOWN);
+          if (it == WAIT_LIMIT - 1) atomicCAS(B.err, 0, ERR_TIMEOUT_TEARDOWN);
         }
       }
     }
@@ -359,7 +353,14 @@ tc_split_kernel(const SplitParams P) {
       int stage = 0, abuf = 0;
       uint32_t phase = 0, aphase = 0;
       bool ok = true;
-      for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+      int jc = 0;
+    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
+      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
+      const SplitJob &P = B.job[jc];
+      const Dims &d = P.d;
+      const int o = d.o, v = d.v;
+      const long long item = gitem - P.item0;
+      (void)v;
         const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
         const int4 tr = P.w.trip[t];
         const int occ[3] = {tr.x, tr.y, tr.z};
@@ -372,11 +373,11 @@ tc_split_kernel(const SplitParams P) {
           for (int jb = 0; ok && jb < nj; ++jb) {
             const int np = c_tjobs[pid][jb].np;
             const int nk = c_tjobs[pid][jb].kind == 0 ? P.kch_p : P.kch_h;
-            if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, P.w.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
+            if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS);
             for (int kc = 0; kc < nk; ++kc) {
-              if (!mbar_wait(&full_bar[stage], phase, &abort_flag, P.w.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
+              if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
               const uint32_t sA = smem_u32(sm + stage * STAGE_BYTES);
               const uint64_t bd = sdesc(sA + S * A_SLICE_BYTES);
@@ -389,7 +390,7 @@ tc_split_kernel(const SplitParams P) {
                   mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > 0 || a > 0) ? 1u : 0u);
                 }
               mma_commit(&empty_bar[stage]);
-              if (++stage == P.stages) { stage = 0; phase ^= 1u; }
+              if (++stage == B.stages) { stage = 0; phase ^= 1u; }
             }
             if (!ok) break;
             mma_commit(&accfull_bar[abuf]);
@@ -402,7 +403,7 @@ tc_split_kernel(const SplitParams P) {
       const uint32_t a = smem_u32(&teardown_bar);
       for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, 0); ++it) {
         if ((it & 255) == 255) __nanosleep(128);
-        if (it == WAIT_LIMIT - 1) atomicCAS(P.w.err, 0, ERR_TIMEOUT_TEARDOWN);
+        if (it == WAIT_LIMIT - 1) atomicCAS(B.err, 0, ERR_TIMEOUT_TEARDOWN);
       }
     }
     __syncwarp();
@@ -415,7 +416,14 @@ tc_split_kernel(const SplitParams P) {
     int abuf = 0;
     uint32_t aphase = 0;
     bool ok = true;
-    for (long long item = blockIdx.x; ok && item < d.n_items; item += gridDim.x) {
+    int jc = 0;
+    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
+      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
+      const SplitJob &P = B.job[jc];
+      const Dims &d = P.d;
+      const int o = d.o, v = d.v;
+      const long long item = gitem - P.item0;
+      (void)v;
       const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
       const int4 tr = P.w.trip[t];
       const int occ[3] = {tr.x, tr.y, tr.z};
@@ -430,7 +438,7 @@ tc_split_kernel(const SplitParams P) {
         for (int jb = 0; jb < nj; ++jb) {
           const TJob J = c_tjobs[pid][jb];
           if (et == 0)
-            epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, P.w.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
+            epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
           epi_bar();
           if (!epi_ok) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -623,10 +631,10 @@ size_t smem_for(int S) {
 }
 
 template <int S>
-cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const SplitParams &P) {
+cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const SplitBatch &b) {
   cudaError_t e = cudaFuncSetAttribute(tc_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(P);
+  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -691,15 +699,11 @@ cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, const Work &w,
-                         int num_sms, cudaStream_t st) {
-  if (S < 2 || S > MAXS) return cudaErrorInvalidValue;
+SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitLayout &L, const Work &w) {
   const int o = d.o, v = d.v;
   const unsigned char *b = (const unsigned char *)ws;
-  SplitParams P{};
+  SplitJob P{};
   P.d = d;
-  P.S = S;
-  P.stages = stages_for(S);
   P.kch_p = (v + KC - 1) / KC;
   P.kch_h = (o + KC - 1) / KC;
   P.T = (v + NT - 1) / NT;
@@ -711,16 +715,27 @@ cudaError_t launch_split(const Dims &d, int S, const Inputs &in, void *ws, const
   P.ovovf = (const float *)(b + L.ovovf);
   P.eps = in.eps;
   P.w = w;
+  return P;
+}
+
+// Launch one persistent kernel over the batch's items (item0 and total_items
+// are filled in here from the jobs' item counts).
+cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st) {
+  if (S < 2 || S > MAXS || b.njobs < 1 || b.njobs > MAX_BATCH) return cudaErrorInvalidValue;
+  long long total = 0;
+  for (int j = 0; j < b.njobs; ++j) { b.job[j].item0 = total; total += b.job[j].d.n_items; }
+  b.total_items = total;
+  b.stages = stages_for(S);
   const size_t smem = smem_for(S);
   cudaError_t e = upload_templates(st);
   if (e != cudaSuccess) return e;
   long long grid = num_sms;
-  if (grid > d.n_items) grid = d.n_items;
+  if (grid > total) grid = total;
   if (grid < 1) return cudaSuccess;
   switch (S) {
-    case 2: e = launch_kernel<2>(grid, smem, st, P); break;
-    case 3: e = launch_kernel<3>(grid, smem, st, P); break;
-    default: e = launch_kernel<4>(grid, smem, st, P); break;
+    case 2: e = launch_kernel<2>(grid, smem, st, b); break;
+    case 3: e = launch_kernel<3>(grid, smem, st, b); break;
+    default: e = launch_kernel<4>(grid, smem, st, b); break;
   }
   return e;
 }
