@@ -68,6 +68,9 @@ typedef struct {
   int default_prec;          /* tc_precision used when a call passes prec < 0 */
   int default_slices;        /* BF16 slices per operand (2..4) used when a call passes slices <= 0 */
   int timeout_ms;            /* limit for tc_wait and for device-side waits; 0 = 60000 */
+  int max_inflight;          /* serving: jobs admitted to the device at once (1..32; 0 = 16) */
+  int max_queue;             /* serving: jobs waiting for admission before tc_submit says TC_EBUSY (0 = 4096) */
+  int iteration_ms;          /* serving: target duration of one batched launch (0 = 50) */
 } tc_options;
 
 typedef struct {
@@ -128,6 +131,68 @@ tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const doub
 tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
                           const double *t2, const tc_ints *ints, int prec, int slices,
                           const int *trip, int n, double *e_out, void *stream, tc_result *out);
+
+/* ------------------------------------------------------------------------
+ * Serving: many (T) jobs of uneven (o, v) and mixed precision on one device.
+ *
+ * tc_submit queues a job and returns at once.  A scheduler owned by the
+ * context admits queued jobs while at most max_inflight are admitted and the
+ * sum of their device footprints (inputs unless resident, work tables, BF16
+ * images) stays within hbm_budget_bytes; admitted jobs are prepared on side
+ * streams while others compute.  Computation proceeds in iterations of about
+ * iteration_ms: each iteration is one persistent multi-job launch (replayed
+ * from a CUDA graph) over a slice of the items of every ready job of one
+ * precision group, the slices shared fairly, so a job submitted while others
+ * run starts within an iteration and small jobs are not stuck behind large
+ * ones.  A job's result does not depend on the other jobs it ran with.
+ * ------------------------------------------------------------------------ */
+#define TC_JOB_DEVICE_INPUTS 1   /* tc_job arrays are DEVICE pointers, kept valid and
+                                    unchanged by the caller until the job completes */
+
+typedef struct {
+  int o, v;
+  const double *eps, *t1, *t2;   /* layouts as for tc_energy */
+  tc_ints ints;
+  int prec;                      /* tc_precision, or < 0 for the context default */
+  int slices;                    /* TC_SPLIT_BF16: 2..4, <= 0 for the default */
+  int flags;                     /* 0: host arrays, copied before tc_submit returns;
+                                    TC_JOB_DEVICE_INPUTS: resident device arrays, not copied */
+} tc_job;
+
+/* Queue a job.  *ticket identifies it in tc_poll / tc_wait / tc_cancel.
+ * TC_EINVAL bad job; TC_ENOMEM its footprint alone exceeds the budget;
+ * TC_EBUSY the queue holds max_queue jobs already. */
+tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket);
+
+/* TC_ENOTREADY while the job is queued or running.  Otherwise fills *out
+ * (e_t; seconds = submit to completion; queue_seconds = submit to its first
+ * iteration), releases the ticket and returns the job's status (TC_OK,
+ * TC_ECANCELLED, or the error it failed with).  Unknown ticket: TC_EINVAL. */
+tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, tc_result *out);
+
+/* As tc_poll, waiting up to timeout_ms (< 0: ctx timeout) for completion;
+ * TC_ETIMEOUT if the job is still pending then (the ticket stays valid). */
+tc_status tc_wait(tc_ctx *ctx, uint64_t ticket, int timeout_ms, tc_result *out);
+
+/* Cancel a job that has not been admitted yet (TC_OK); TC_EBUSY once it is
+ * admitted; TC_EINVAL unknown ticket. */
+tc_status tc_cancel(tc_ctx *ctx, uint64_t ticket);
+
+typedef struct {
+  uint64_t submitted, completed, failed, cancelled;
+  uint64_t queued, inflight;      /* now */
+  uint64_t iterations, graph_launches, batched_jobs;   /* batched_jobs: sum over iterations of jobs per launch */
+  size_t reserved_bytes;          /* device bytes held by admitted jobs now */
+} tc_serve_stats;
+tc_status tc_serve_stats_get(tc_ctx *ctx, tc_serve_stats *out);
+
+/* Host-side fault injection for tests (nothing is faulted on the device):
+ * TC_FAULT_ALLOC: the next admission behaves as if device allocation failed
+ * (that job fails with TC_ENOMEM); TC_FAULT_STALL: the scheduler pauses for
+ * param milliseconds before its next iteration. */
+#define TC_FAULT_ALLOC 1
+#define TC_FAULT_STALL 2
+tc_status tc_inject_fault(tc_ctx *ctx, int kind, int param);
 
 /* Size of the library's static device scratch array used by
  * tc_energy_dev_noalloc (held on every GPU that loads the library). */

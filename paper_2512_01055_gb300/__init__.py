@@ -18,7 +18,10 @@ TC_FP64, TC_SPLIT_BF16 = 0, 1
 
 #: Every symbol include/tc.h declares (the CPU test checks the library exports them).
 EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
-           "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc", "tc_triplets_dev")
+           "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc", "tc_triplets_dev", "tc_submit", "tc_poll",
+           "tc_wait", "tc_cancel", "tc_serve_stats_get", "tc_inject_fault")
+TC_JOB_DEVICE_INPUTS = 1
+TC_FAULT_ALLOC, TC_FAULT_STALL = 1, 2
 
 #: TC_NOALLOC_SCRATCH_BYTES of include/tc.h
 NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -27,11 +30,24 @@ NOALLOC_SCRATCH_BYTES = 8 << 20
 class tc_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("default_prec", ctypes.c_int), ("default_slices", ctypes.c_int),
-                ("timeout_ms", ctypes.c_int)]
+                ("timeout_ms", ctypes.c_int), ("max_inflight", ctypes.c_int), ("max_queue", ctypes.c_int),
+                ("iteration_ms", ctypes.c_int)]
 
 
 class tc_ints(ctypes.Structure):
     _fields_ = [("ovvv", ctypes.c_void_p), ("ovoo", ctypes.c_void_p), ("ovov", ctypes.c_void_p)]
+
+
+class tc_job(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int), ("v", ctypes.c_int), ("eps", ctypes.c_void_p), ("t1", ctypes.c_void_p),
+                ("t2", ctypes.c_void_p), ("ints", tc_ints), ("prec", ctypes.c_int), ("slices", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class tc_serve_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "cancelled", "queued", "inflight",
+                                               "iterations", "graph_launches", "batched_jobs")] + \
+               [("reserved_bytes", ctypes.c_size_t)]
 
 
 class tc_result(ctypes.Structure):
@@ -82,6 +98,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_triplets_dev.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(tc_ints), i, i, vp, i, vp, vp,
                                     ctypes.POINTER(tc_result)]
     lib.tc_triplets_dev.restype = i
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.tc_submit.argtypes = [vp, ctypes.POINTER(tc_job), u64p]
+    lib.tc_submit.restype = i
+    lib.tc_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(tc_result)]
+    lib.tc_poll.restype = i
+    lib.tc_wait.argtypes = [vp, ctypes.c_uint64, i, ctypes.POINTER(tc_result)]
+    lib.tc_wait.restype = i
+    lib.tc_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.tc_cancel.restype = i
+    lib.tc_serve_stats_get.argtypes = [vp, ctypes.POINTER(tc_serve_stats)]
+    lib.tc_serve_stats_get.restype = i
+    lib.tc_inject_fault.argtypes = [vp, i, i]
+    lib.tc_inject_fault.restype = i
     del d, dp
     _lib = lib
     return lib
@@ -96,10 +125,12 @@ def status_str(s: int) -> str:
 # ---------------------------------------------------------------------------
 
 def tc_init(device: int = 0, hbm_budget_bytes: int = 0, default_prec: int = TC_FP64,
-            default_slices: int = 3, timeout_ms: int = 0) -> ctypes.c_void_p:
+            default_slices: int = 3, timeout_ms: int = 0, max_inflight: int = 0, max_queue: int = 0,
+            iteration_ms: int = 0) -> ctypes.c_void_p:
     lib = load()
     ctx = ctypes.c_void_p()
-    opt = tc_options(device, hbm_budget_bytes, default_prec, default_slices, timeout_ms)
+    opt = tc_options(device, hbm_budget_bytes, default_prec, default_slices, timeout_ms, max_inflight, max_queue,
+                     iteration_ms)
     s = lib.tc_init(ctypes.byref(ctx), ctypes.byref(opt))
     if s != TC_OK:
         raise TcError(s, "tc_init failed")
@@ -200,3 +231,44 @@ def tc_energy_dev_noalloc(o, v, eps, t1, t2, ovvv, ovoo, ovov, e_t, e_ijk=None, 
                                      _ptr_dev(e_t), _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), buf, 256)
     if s != TC_OK:
         raise TcError(s, buf.value.decode())
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+
+def tc_submit(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices=0, device_inputs=False) -> int:
+    """Queue one job; host numpy arrays are copied before return, device tensors stay resident (caller keeps them)."""
+    ptr = _ptr_dev if device_inputs else _ptr_np
+    job = tc_job(o, v, ptr(eps), ptr(t1), ptr(t2), tc_ints(ptr(ovvv), ptr(ovoo), ptr(ovov)), prec, slices,
+                 TC_JOB_DEVICE_INPUTS if device_inputs else 0)
+    ticket = ctypes.c_uint64()
+    s = load().tc_submit(ctx, ctypes.byref(job), ctypes.byref(ticket))
+    if s != TC_OK:
+        raise TcError(s, "tc_submit refused the job")
+    return ticket.value
+
+
+def tc_poll(ctx, ticket):
+    """(status, tc_result); status TC_ENOTREADY while the job is pending."""
+    res = tc_result()
+    return load().tc_poll(ctx, ticket, ctypes.byref(res)), res
+
+
+def tc_wait(ctx, ticket, timeout_ms=-1):
+    res = tc_result()
+    return load().tc_wait(ctx, ticket, timeout_ms, ctypes.byref(res)), res
+
+
+def tc_cancel(ctx, ticket) -> int:
+    return load().tc_cancel(ctx, ticket)
+
+
+def tc_serve_stats_get(ctx) -> tc_serve_stats:
+    st = tc_serve_stats()
+    _check(ctx, load().tc_serve_stats_get(ctx, ctypes.byref(st)))
+    return st
+
+
+def tc_inject_fault(ctx, kind, param=0) -> int:
+    return load().tc_inject_fault(ctx, kind, param)

@@ -1,5 +1,6 @@
 // C ABI of the (T) library (include/tc.h): argument checks, HBM admission,
-// device workspace reuse, work tables, launches and the final read-back.
+// device workspace reuse, work tables, launches and the final read-back of
+// the blocking entry points.  The serving entry points are in tc_serve.cu.
 #include <algorithm>
 #include <chrono>
 #include <cstdarg>
@@ -10,49 +11,9 @@
 #include <vector>
 
 #include "../../include/tc.h"
+#include "tc_ctx.h"
 #include "tc_internal.cuh"
-
-namespace {
-
-struct DevBuf {
-  void *p = nullptr;
-  size_t cap = 0;
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= cap) return cudaSuccess;
-    if (p) { cudaFree(p); p = nullptr; cap = 0; }
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e == cudaSuccess) cap = bytes; else p = nullptr;
-    return e;
-  }
-  void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
-};
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-struct Layout {            // byte offsets inside the per-job workspace
-  size_t partial, e_trip, out, counter, total;
-};
-
-}  // namespace
-
-struct tc_ctx {
-  int device = 0;
-  size_t budget = 0;
-  int default_prec = TC_FP64;
-  int default_slices = 3;
-  int timeout_ms = 60000;
-  int num_sms = 0;
-  std::mutex mu;
-  std::string err;
-  cudaStream_t stream = nullptr;
-  DevBuf ws;                 // work tables + partials, reused across calls
-  DevBuf ws_split;           // BF16 slices and FP32 copies of the split path
-  DevBuf tables;             // triplet and orbit tables of the last shape
-  int tab_o = -1, tab_v = -1, tab_nt = -1;
-  DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies
-  double *host_out = nullptr;                               // pinned read-back slot
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // kernel timing
-};
+#include "tc_plan.cuh"
 
 namespace {
 
@@ -73,74 +34,6 @@ tc_status fail(tc_ctx *ctx, tc_status s, const char *fmt, ...) {
       return fail(ctx, TC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
                   __FILE__, __LINE__);                                                      \
   } while (0)
-
-tc::Dims make_dims(int o, int v, int nt, int n_trip_override = -1) {
-  tc::Dims d{};
-  d.o = o;
-  d.v = v;
-  d.nt = nt;
-  d.ntiles = (v + nt - 1) / nt;
-  const long long T = d.ntiles;
-  d.n_trip = n_trip_override >= 0 ? n_trip_override : (int)((long long)o * (o + 1) * (o + 2) / 6 - o);
-  d.n_orb = (int)(T * (T + 1) * (T + 2) / 6);
-  const long long pairs = (long long)d.n_trip * d.n_orb;
-  const long long target = 4LL << 20;   // at most ~4M partials
-  d.orb_per_item = (int)std::max<long long>(1, (pairs + target - 1) / target);
-  d.items_per_trip = (d.n_orb + d.orb_per_item - 1) / d.orb_per_item;
-  d.n_items = (long long)d.n_trip * d.items_per_trip;
-  return d;
-}
-
-Layout make_layout(const tc::Dims &d) {
-  Layout L{};
-  size_t off = 0;
-  L.partial = off; off = align256(off + sizeof(double) * (size_t)std::max<long long>(1, d.n_items));
-  L.e_trip = off;  off = align256(off + sizeof(double) * (size_t)std::max(1, d.n_trip));
-  L.out = off;     off = align256(off + 4 * sizeof(double));
-  L.counter = off; off = align256(off + 2 * sizeof(unsigned));
-  L.total = off;
-  return L;
-}
-
-size_t table_bytes(const tc::Dims &d) {
-  return align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) + sizeof(int4) * (size_t)std::max(1, d.n_orb);
-}
-
-// Triplet and orbit tables.  subset (optional): the triplets to process
-// instead of all of them (already checked, all-equal triplets removed).
-tc_status ensure_tables(tc_ctx *ctx, const tc::Dims &d, cudaStream_t st, const int4 **trip, const int4 **orb,
-                        const std::vector<int4> *subset) {
-  const size_t tb = table_bytes(d);
-  if (subset || !(ctx->tab_o == d.o && ctx->tab_v == d.v && ctx->tab_nt == d.nt && ctx->tables.cap >= tb)) {
-    std::vector<int4> h(tb / sizeof(int4) + 1);
-    int4 *ht = h.data();
-    int n = 0;
-    if (subset) {
-      for (const int4 &t : *subset) ht[n++] = t;
-    } else {
-      for (int i = 0; i < d.o; ++i)
-        for (int j = 0; j <= i; ++j)
-          for (int k = 0; k <= j; ++k) {
-            if (i == k) continue;                     // i == j == k: zero contribution
-            ht[n++] = make_int4(i, j, k, 2 - (i == j) - (j == k));
-          }
-    }
-    int4 *ho = ht + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)) / sizeof(int4);
-    int m = 0;
-    for (int P = 0; P < d.ntiles; ++P)
-      for (int Q = 0; Q <= P; ++Q)
-        for (int R = 0; R <= Q; ++R) ho[m++] = make_int4(P, Q, R, 0);
-    if (n != d.n_trip || m != d.n_orb) return fail(ctx, TC_EINTERNAL, "work table size mismatch");
-    TC_CUDA(ctx, ctx->tables.ensure(tb));
-    TC_CUDA(ctx, cudaMemcpyAsync(ctx->tables.p, ht, tb, cudaMemcpyHostToDevice, st));
-    TC_CUDA(ctx, cudaStreamSynchronize(st));
-    if (subset) { ctx->tab_o = -1; ctx->tab_v = -1; ctx->tab_nt = -1; }   // not the full table
-    else { ctx->tab_o = d.o; ctx->tab_v = d.v; ctx->tab_nt = d.nt; }
-  }
-  *trip = (const int4 *)ctx->tables.p;
-  *orb = (const int4 *)((char *)ctx->tables.p + align256(sizeof(int4) * (size_t)std::max(1, d.n_trip)));
-  return TC_OK;
-}
 
 tc_status check_args(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
                      const tc_ints *ints, int *prec, int *slices) {
@@ -167,25 +60,25 @@ double alg_flops(int o, int v) {
 }
 
 // The hot path on device-resident inputs.  Caller holds ctx->mu.
+// subset (optional): process these triplets only; e_sub receives their sums.
 tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, int slices, double *e_ijk_dev,
                      cudaStream_t st, tc_result *out, const std::vector<int4> *subset = nullptr,
                      std::vector<double> *e_sub = nullptr) {
   const bool split = (prec == TC_SPLIT_BF16);
   const int nt = split ? tc::split_tile() : tc::fp64_tile();
-  const tc::Dims d = make_dims(o, v, nt, subset ? (int)subset->size() : -1);
-  const Layout L = make_layout(d);
+  const tc::Dims d = tc::plan::make_dims(o, v, nt, subset ? (int)subset->size() : -1);
+  const tc::plan::Layout L = tc::plan::make_layout(d);
   const tc::SplitLayout SL = split ? tc::split_layout(o, v, slices) : tc::SplitLayout{};
-  const size_t need = L.total + table_bytes(d) + SL.total;
+  const size_t need = L.total + SL.total;
   if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "workspace %zu B exceeds budget %zu B", need, ctx->budget);
-  const int4 *trip = nullptr, *orb = nullptr;
-  tc_status s = ensure_tables(ctx, d, st, &trip, &orb, subset);
-  if (s != TC_OK) return s;
   TC_CUDA(ctx, ctx->ws.ensure(L.total));
   if (split) TC_CUDA(ctx, ctx->ws_split.ensure(SL.total));
   char *base = (char *)ctx->ws.p;
+  const std::vector<int4> tab = tc::plan::tables(d, L, subset);
+  TC_CUDA(ctx, cudaMemcpyAsync(base + L.trip, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
   tc::Work w{};
-  w.trip = trip;
-  w.orb = orb;
+  w.trip = (const int4 *)(base + L.trip);
+  w.orb = (const int4 *)(base + L.orb);
   w.partial = (double *)(base + L.partial);
   w.counter = (unsigned *)(base + L.counter);
   w.err = (int *)(base + L.counter + sizeof(unsigned));
@@ -217,7 +110,7 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
       b.njobs = 1;
       b.total_items = d.n_items;
       b.counter = w.counter;
-      b.job[0] = tc::FpJob{d, in, w, 0};
+      b.job[0] = tc::FpJob{d, in, w, 0, 0};
       TC_CUDA(ctx, tc::launch_fp64(b, (int)grid, st));
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
@@ -289,8 +182,8 @@ size_t tc_workspace_bytes(int o, int v, int prec, int slices) {
   if (o <= 0 || v <= 0) return 0;
   const bool split = (prec == TC_SPLIT_BF16);
   if (split && slices <= 0) slices = 3;
-  const tc::Dims d = make_dims(o, v, split ? tc::split_tile() : tc::fp64_tile());
-  return make_layout(d).total + table_bytes(d) + (split ? tc::split_layout(o, v, slices).total : 0);
+  const tc::Dims d = tc::plan::make_dims(o, v, split ? tc::split_tile() : tc::fp64_tile());
+  return tc::plan::make_layout(d).total + (split ? tc::split_layout(o, v, slices).total : 0);
 }
 
 tc_status tc_init(tc_ctx **out, const tc_options *opt) {
@@ -304,6 +197,9 @@ tc_status tc_init(tc_ctx **out, const tc_options *opt) {
     ctx->default_prec = opt->default_prec;
     ctx->default_slices = opt->default_slices > 0 ? opt->default_slices : 3;
     ctx->timeout_ms = opt->timeout_ms > 0 ? opt->timeout_ms : 60000;
+    if (opt->max_inflight > 0) ctx->max_inflight = std::min(opt->max_inflight, tc::MAX_BATCH);
+    if (opt->max_queue > 0) ctx->max_queue = opt->max_queue;
+    if (opt->iteration_ms > 0) ctx->iteration_ms = opt->iteration_ms;
   }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -331,11 +227,11 @@ tc_status tc_init(tc_ctx **out, const tc_options *opt) {
 
 void tc_finalize(tc_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->server) tc::server_destroy(ctx->server);   // stops the scheduler, releases its jobs
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->ws.release();
   ctx->ws_split.release();
-  ctx->tables.release();
   ctx->in_eps.release(); ctx->in_t1.release(); ctx->in_t2.release();
   ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
@@ -378,6 +274,9 @@ tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const do
     const int i = trip[3 * m], j = trip[3 * m + 1], k = trip[3 * m + 2];
     if (!(o > i && i >= j && j >= k && k >= 0))
       return fail(ctx, TC_EINVAL, "triplet %d = (%d, %d, %d) is not o > i >= j >= k >= 0", m, i, j, k);
+  }
+  for (int m = 0; m < n; ++m) {
+    const int i = trip[3 * m], j = trip[3 * m + 1], k = trip[3 * m + 2];
     e_out[m] = 0.0;
     if (i == k) continue;
     sub.push_back(make_int4(i, j, k, 2 - (i == j) - (j == k)));

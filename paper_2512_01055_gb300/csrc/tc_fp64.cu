@@ -60,7 +60,7 @@ tc_fp64_kernel(const __grid_constant__ FpBatch B) {
     const Dims &d = B.job[jc].d;
     const Inputs &in = B.job[jc].in;
     const Work &w = B.job[jc].w;
-    const long long item = gitem - B.job[jc].item0;
+    const long long item = gitem - B.job[jc].item0 + B.job[jc].item_base;
     const int o = d.o, v = d.v;
     const long long vv = (long long)v * v;
     const int t = (int)(item / d.items_per_trip);
@@ -232,6 +232,16 @@ cudaError_t fp64_blocks_per_sm(int *n) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tc_fp64_kernel, THREADS, fp64_smem_bytes());
   if (e == cudaSuccess && *n < 1) *n = 1;
   return e;
+}
+
+void fp64_node_params(const FpBatch &b, int grid, void **args, cudaKernelNodeParams *p) {
+  args[0] = (void *)&b;
+  *p = cudaKernelNodeParams{};
+  p->func = (void *)tc_fp64_kernel;
+  p->gridDim = dim3(grid);
+  p->blockDim = dim3(THREADS);
+  p->sharedMemBytes = (unsigned)fp64_smem_bytes();
+  p->kernelParams = args;
 }
 
 cudaError_t launch_fp64(const FpBatch &b, int grid, cudaStream_t st) {

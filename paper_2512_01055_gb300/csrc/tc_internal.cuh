@@ -64,7 +64,8 @@ struct FpJob {
   Dims d;
   Inputs in;
   Work w;
-  long long item0;     // first global item of this job
+  long long item0;     // first global item of this job in the launch
+  long long item_base; // the job's own index of that item (a launch may run a slice of a job)
 };
 struct FpBatch {
   int njobs;
@@ -76,6 +77,9 @@ int fp64_tile();
 size_t fp64_smem_bytes();
 cudaError_t fp64_blocks_per_sm(int *n);
 cudaError_t launch_fp64(const FpBatch &b, int grid, cudaStream_t st);
+// Kernel-node parameters of one FP64 launch (for CUDA graphs); args[0] must
+// point to b while the parameters are used.
+void fp64_node_params(const FpBatch &b, int grid, void **args, cudaKernelNodeParams *p);
 
 // ---------------------------------------------------------------- split path
 // Byte offsets of the BF16 operand images and FP32 copies inside a job's
@@ -93,7 +97,9 @@ struct SplitJob {
   const float *t1f, *ovovf;
   const double *eps;
   Work w;
-  long long item0;
+  long long item0;       // first global item of this job in the launch
+  long long item_base;   // the job's own index of that item
+  long long n_run;       // items of this job in the launch (0: all n_items)
 };
 struct SplitBatch {
   int njobs;
@@ -107,6 +113,9 @@ SplitLayout split_layout(int o, int v, int S);
 cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st);
 SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitLayout &L, const Work &w);
 cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st);
+// Prepare b (item offsets, stages) and fill kernel-node parameters of the launch
+// launch_split would make; also performs launch_split's one-time set-up.
+cudaError_t split_node_params(SplitBatch &b, int S, int grid, void **args, cudaKernelNodeParams *p, cudaStream_t st);
 
 // ---------------------------------------------------------------- reduction
 struct RedJob {

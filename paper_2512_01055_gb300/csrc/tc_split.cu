@@ -283,7 +283,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const SplitJob &P = B.job[jc];
       const Dims &d = P.d;
       const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0;
+      const long long item = gitem - P.item0 + P.item_base;
       (void)v;
       const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
       const int4 tr = P.w.trip[t];
@@ -359,7 +359,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const SplitJob &P = B.job[jc];
       const Dims &d = P.d;
       const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0;
+      const long long item = gitem - P.item0 + P.item_base;
       (void)v;
         const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
         const int4 tr = P.w.trip[t];
@@ -422,7 +422,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const SplitJob &P = B.job[jc];
       const Dims &d = P.d;
       const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0;
+      const long long item = gitem - P.item0 + P.item_base;
       (void)v;
       const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
       const int4 tr = P.w.trip[t];
@@ -720,10 +720,47 @@ SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitL
 
 // Launch one persistent kernel over the batch's items (item0 and total_items
 // are filled in here from the jobs' item counts).
+template <int S>
+void node_params(const SplitBatch &b, int grid, void **args, cudaKernelNodeParams *p) {
+  args[0] = (void *)&b;
+  *p = cudaKernelNodeParams{};
+  p->func = (void *)tc_split_kernel<S>;
+  p->gridDim = dim3(grid);
+  p->blockDim = dim3(THREADS);
+  p->sharedMemBytes = (unsigned)smem_for(S);
+  p->kernelParams = args;
+}
+
+cudaError_t split_node_params(SplitBatch &b, int S, int grid, void **args, cudaKernelNodeParams *p, cudaStream_t st) {
+  if (S < 2 || S > MAXS || b.njobs < 1 || b.njobs > MAX_BATCH) return cudaErrorInvalidValue;
+  long long total = 0;
+  for (int j = 0; j < b.njobs; ++j) {
+    b.job[j].item0 = total;
+    total += b.job[j].n_run > 0 ? b.job[j].n_run : b.job[j].d.n_items;
+  }
+  b.total_items = total;
+  b.stages = stages_for(S);
+  cudaError_t e = upload_templates(st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_for(S);
+  switch (S) {
+    case 2: e = cudaFuncSetAttribute(tc_split_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            node_params<2>(b, grid, args, p); break;
+    case 3: e = cudaFuncSetAttribute(tc_split_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            node_params<3>(b, grid, args, p); break;
+    default: e = cudaFuncSetAttribute(tc_split_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+             node_params<4>(b, grid, args, p); break;
+  }
+  return e;
+}
+
 cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st) {
   if (S < 2 || S > MAXS || b.njobs < 1 || b.njobs > MAX_BATCH) return cudaErrorInvalidValue;
   long long total = 0;
-  for (int j = 0; j < b.njobs; ++j) { b.job[j].item0 = total; total += b.job[j].d.n_items; }
+  for (int j = 0; j < b.njobs; ++j) {
+    b.job[j].item0 = total;
+    total += b.job[j].n_run > 0 ? b.job[j].n_run : b.job[j].d.n_items;
+  }
   b.total_items = total;
   b.stages = stages_for(S);
   const size_t smem = smem_for(S);
