@@ -162,19 +162,112 @@ def reference_arm(args, name, o, v, flops, metric):
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def serving_requests(n, fp64_share, slices):
+    """The seeded request stream: (o, v, seed, prec, slices) per request and Poisson arrival offsets (s, rate 1)."""
+    reqs = []
+    for r in range(n):
+        o, v = synth.serving_request_shape(r)
+        u = float(synth.uniform(synth.SERVING_SEED_BASE + r, 98, 0, 1)[0])
+        fp64 = u < fp64_share
+        reqs.append((o, v, synth.SERVING_SEED_BASE + r, 0 if fp64 else 1, 0 if fp64 else slices))
+    gaps = -np.log1p(-synth.uniform(synth.SERVING_ARRIVAL_SEED, 1, 0, n))
+    return reqs, np.cumsum(gaps)
+
+
+def serving(args):
+    """Continuous-batching service on one GPU: p50/p99 latency and jobs/s at a stated arrival rate."""
+    import threading
+    import torch
+    import paper_2512_01055_gb300 as tc
+    from paper_2512_01055_gb300 import build as tcbuild
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(0)
+    tcbuild.build()
+    reqs, offs = serving_requests(args.requests, args.fp64_share, args.slices)
+    # service-time estimate from the measured single-job rates (FP64 ~0.9 TF/s, split ~50 TF/s at s=3)
+    est = [alg_flops(o, v) / (0.9e12 if p == 0 else 50e12 * 6.0 / (s * (s + 1) / 2)) for (o, v, _, p, s) in reqs]
+    capacity = 1.0 / max(1e-9, float(np.mean(est)))
+    rate = args.rate if args.rate > 0 else args.load * capacity
+    arrivals = offs / rate
+    t_gen = time.perf_counter()
+    devs = [synth.device_job(synth.make_amplitudes(o, v, seed)) for (o, v, seed, _, _) in reqs]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    ctx = tc.tc_init(0, max_inflight=16, iteration_ms=50)
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+    done = threading.Event()
+
+    def collector():
+        for n in range(len(reqs)):
+            while tickets[n] is None:
+                time.sleep(0.001)
+            st, res = tc.tc_wait(ctx, tickets[n], 24 * 3600 * 1000)
+            results[n] = (st, res.seconds, res.queue_seconds, res.e_t)
+        done.set()
+
+    th = threading.Thread(target=collector)
+    th.start()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for n, (o, v, _, prec, s) in enumerate(reqs):
+            delay = arrivals[n] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            d = devs[n]
+            tickets[n] = tc.tc_submit(ctx, o, v, d["eps"], d["t1"], d["t2"], d["ovvv"], d["ovoo"], d["ovov"],
+                                      prec=prec, slices=s, device_inputs=True)
+        done.wait()
+        makespan = time.perf_counter() - t0
+    th.join()
+    stats = tc.tc_serve_stats_get(ctx)
+    tc.tc_finalize(ctx)
+    ok = [r for r in results if r[0] == tc.TC_OK]
+    lat = np.array([r[1] for r in ok])
+    que = np.array([r[2] for r in ok])
+    flops = sum(alg_flops(o, v) for (o, v, _, _, _) in reqs)
+    by = lambda p: np.array([r[1] for r, q in zip(results, reqs) if q[3] == p and r[0] == tc.TC_OK])
+    out = {
+        "metric": "serving latency", "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "value": float(np.percentile(lat, 99)), "p50_s": float(np.percentile(lat, 50)),
+        "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+        "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
+        "jobs_per_s": len(ok) / makespan, "tflops_aggregate": flops / makespan / 1e12,
+        "rate_per_s": rate, "offered_load": rate / capacity, "requests": len(reqs), "completed": len(ok),
+        "fp64_requests": int(sum(1 for q in reqs if q[3] == 0)),
+        "p50_fp64_s": float(np.percentile(by(0), 50)) if len(by(0)) else None,
+        "p50_split_s": float(np.percentile(by(1), 50)) if len(by(1)) else None,
+        "makespan_s": makespan, "input_generation_s": t_gen,
+        "iterations": stats.iterations, "graph_launches": stats.graph_launches,
+        "mean_jobs_per_launch": stats.batched_jobs / max(1, stats.iterations),
+        "clocks": clk.summary(), "data": "synthetic (seeded request stream, inputs resident on the device)",
+        "config": {"workload": "serving", "o": "U{6..32}", "v": "round(o*U[6,12])", "Q": "3(o+v)",
+                   "fp64_share": args.fp64_share, "slices": args.slices, "prefix_of_stream": args.requests,
+                   "arrivals": "Poisson (seeded)"},
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single_o20_v200", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="single_o20_v200", choices=sorted(synth.WORKLOADS) + ["serving"])
     ap.add_argument("--prec", default="both", choices=["both", "split", "fp64"])
     ap.add_argument("--slices", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=24, help="serving: requests of the seeded stream to run")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: --load x capacity)")
+    ap.add_argument("--load", type=float, default=0.5, help="serving: offered load relative to estimated capacity")
+    ap.add_argument("--fp64-share", type=float, default=0.5, help="serving: fraction of FP64 requests")
     args = ap.parse_args()
+    if args.workload == "serving":
+        return serving(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
