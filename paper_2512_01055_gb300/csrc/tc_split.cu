@@ -60,6 +60,10 @@ constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*W
 constexpr int W_BYTES = 6 * WBLK * 4;
 constexpr int MAX_JOBS = 72;
 constexpr long long WAIT_LIMIT = 1LL << 26;
+// Longest run of K blocks accumulated in one tensor-core accumulator.  The FP32
+// accumulation along K rounds systematically, so longer products are split into
+// chains of at most KCHAIN blocks (256 K values), each drained and added into W.
+constexpr int KCHAIN = 16;
 
 constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL = 13,
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
@@ -373,10 +377,13 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
           for (int jb = 0; ok && jb < nj; ++jb) {
             const int np = c_tjobs[pid][jb].np;
             const int nk = c_tjobs[pid][jb].kind == 0 ? P.kch_p : P.kch_h;
+            const int nchain = (nk + KCHAIN - 1) / KCHAIN;
+            for (int ch = 0; ok && ch < nchain; ++ch) {
+            const int kc0 = ch * nk / nchain, kc1 = (ch + 1) * nk / nchain;
             if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS);
-            for (int kc = 0; kc < nk; ++kc) {
+            for (int kc = kc0; kc < kc1; ++kc) {
               if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
               const uint32_t sA = smem_u32(sm + stage * STAGE_BYTES);
@@ -387,7 +394,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
                 for (int a = 0; a < S; ++a) {
                   const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + h * (A_SLICE_BYTES / 2));
                   const uint32_t dcol = dbase + (uint32_t)(h * S * 32 + a * np * NT);
-                  mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > 0 || a > 0) ? 1u : 0u);
+                  mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > kc0 || a > 0) ? 1u : 0u);
                 }
               mma_commit(&empty_bar[stage]);
               if (++stage == B.stages) { stage = 0; phase ^= 1u; }
@@ -395,6 +402,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
             if (!ok) break;
             mma_commit(&accfull_bar[abuf]);
             if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+            }
           }
         }
       }
@@ -437,6 +445,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
         const int nj = c_ntjobs[pid];
         for (int jb = 0; jb < nj; ++jb) {
           const TJob J = c_tjobs[pid][jb];
+          const int nchain = ((J.kind == 0 ? P.kch_p : P.kch_h) + KCHAIN - 1) / KCHAIN;
+          for (int ch = 0; ch < nchain; ++ch) {
           if (et == 0)
             epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
           epi_bar();
@@ -477,6 +487,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
           epi_bar();                             // all loads and W updates of this job are done
           if (et == 0) mbar_arrive(&accempty_bar[abuf]);
           if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
+          }
+          if (!ok) break;
         }
         if (!ok) break;
 
