@@ -35,6 +35,18 @@ struct Dims {
   long long n_items;
 };
 
+// Work item q of a job (its sequence number in launch order) -> (triplet t,
+// orbit chunk c).  Items run chunk-major: the CTAs in flight at one time work
+// on the same few tile triples for many triplets, so the operand tiles they
+// stream are shared through L2.  The item's partial keeps the triplet-major
+// slot t * items_per_trip + c, so the order of the final reduction (and every
+// bit of the result) does not depend on the launch order.
+__host__ __device__ inline long long item_slot(const Dims &d, long long q, int &t, int &chunk) {
+  chunk = (int)(q / d.n_trip);
+  t = (int)(q % d.n_trip);
+  return (long long)t * d.items_per_trip + chunk;
+}
+
 struct Inputs {        // device pointers, layouts as in include/tc.h
   const double *eps, *t1, *t2, *ovvv, *ovoo, *ovov;
 };

@@ -52,7 +52,16 @@ constexpr int A_SLICE_BYTES = 256 * KC * 2;
 constexpr int B_PANEL_BYTES = NT * KC * 2;
 constexpr int MAXS = 4;
 constexpr int MAX_STAGES = 8;
-constexpr int THREADS = 320;
+// Copy issue: one warp completes about one pipeline stage per ~0.36 us however
+// many stages it has in flight, while several issuing warps overlap.  NPROD
+// producer warps (warp 0 and warps 10, 11, ...) therefore fill the stages
+// round-robin.
+// MMA issue: one issuing thread spends ~210 ns on the six MMAs of a K block
+// (N = 96, 64, 32 per half); two issuing warps, one per 128-row half of the A
+// tile, bring it to ~150 ns.  Warp 1 issues half 0 and warp 12 half 1.
+constexpr int NPROD = 3;
+constexpr int MMA_WARP1 = 10 + (NPROD - 1);
+constexpr int THREADS = 32 * (MMA_WARP1 + 1);
 constexpr int EPI_THREADS = 256;
 constexpr int EPI_WARPS = EPI_THREADS / 32;
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
@@ -170,6 +179,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
+__device__ __forceinline__ void prod_bar() { asm volatile("bar.sync 2, %0;" :: "n"(NPROD * 32) : "memory"); }
 
 // Distinct tile block holding each formal permutation of the orbit's tile triple.
 __host__ __device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6]) {
@@ -248,18 +258,22 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
   float *Wsm = (float *)(sm + B.stages * STAGE_BYTES);
 
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
-  __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar;
+  __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   __shared__ int epi_ok;
   __shared__ double red[EPI_WARPS];
+  __shared__ long long last_seq[NPROD][MAX_STAGES];   // per producer: its latest copy into each stage
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  if (tid < NPROD * MAX_STAGES) last_seq[tid / MAX_STAGES][tid % MAX_STAGES] = -1;
   if (tid == 0) {
-    for (int s = 0; s < B.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&accfull_bar[b], 1); mbar_init(&accempty_bar[b], 1); }
-    mbar_init(&teardown_bar, 1);
+    // a stage is free, and an accumulator buffer full, once both MMA warps committed
+    for (int s = 0; s < B.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 2); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accfull_bar[b], 2); mbar_init(&accempty_bar[b], 1); }
+    mbar_init(&teardown_bar[0], 1);
+    mbar_init(&teardown_bar[1], 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -268,7 +282,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
                  :: "r"(smem_u32(&tmem_base_sh)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (warp >= 2) {
+  if (warp >= 2 && warp < 10) {
     for (int e = tid - 64; e < 6 * WBLK; e += EPI_THREADS) Wsm[e] = 0.f;
   }
   __syncthreads();
@@ -276,10 +290,15 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
   const uint32_t tbase = tmem_base_sh;
   constexpr int BUFCOLS = 2 * S * 32;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer (whole warp)
+  if (warp == 0 || (warp >= 10 && warp < MMA_WARP1)) {
+    // ------------------------------------------------------------ bulk-copy producers (whole warps)
+    // Every producer walks the same sequence of K blocks; producer pw fills the
+    // blocks whose sequence number is pw modulo NPROD.
+    const int pw = warp == 0 ? 0 : warp - 9;
     int stage = 0;
     uint32_t phase = 0;
+    long long seq = 0;
+    int rr = 0;                               // seq modulo NPROD
     bool ok = true;
     int jc = 0;
     for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
@@ -289,7 +308,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const int o = d.o, v = d.v;
       const long long item = gitem - P.item0 + P.item_base;
       (void)v;
-      const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+      int t, chunk;
+      item_slot(d, item, t, chunk);
       const int4 tr = P.w.trip[t];
       const int occ[3] = {tr.x, tr.y, tr.z};
       const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
@@ -316,33 +336,45 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
             const int bt = tl[J.ptpos[bpn]], b0 = occ[J.p0pos[bpn]], b1 = occ[J.p1pos[bpn]];
             srcB = (J.kind == 0 ? P.imgB_p : P.imgB_h) + ((size_t)((b0 * o + b1) * T + bt) * nk * S + bq) * B_PANEL_BYTES;
           }
-          for (int kc = 0; kc < nk; ++kc) {
-            int got = 1;
-            if (lane == 0) {
-              got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
-              if (got) mbar_expect_tx(&full_bar[stage], bytes);
+          for (int kc = 0; kc < nk; ++kc, ++seq) {
+            const bool mine = rr == pw;
+            if (++rr == NPROD) rr = 0;
+            if (mine) {
+              int got = 1;
+              if (lane == 0) {
+                got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
+                if (got) {
+                  last_seq[pw][stage] = seq;
+                  mbar_expect_tx(&full_bar[stage], bytes);
+                }
+              }
+              got = __shfl_sync(0xffffffffu, got, 0);
+              if (!got) { ok = false; break; }
+              unsigned char *sA = sm + stage * STAGE_BYTES;
+              unsigned char *sB = sA + S * A_SLICE_BYTES;
+              if (lane == 0) {
+                bulk_load(sA, srcA + (size_t)kc * S * A_SLICE_BYTES, S * A_SLICE_BYTES, &full_bar[stage]);
+              } else if (bload) {
+                bulk_load(sB + (bq * np + bpn) * B_PANEL_BYTES, srcB + (size_t)kc * S * B_PANEL_BYTES, B_PANEL_BYTES,
+                          &full_bar[stage]);
+              }
+              __syncwarp();
             }
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (!got) { ok = false; break; }
-            unsigned char *sA = sm + stage * STAGE_BYTES;
-            unsigned char *sB = sA + S * A_SLICE_BYTES;
-            if (lane == 0) {
-              bulk_load(sA, srcA + (size_t)kc * S * A_SLICE_BYTES, S * A_SLICE_BYTES, &full_bar[stage]);
-            } else if (bload) {
-              bulk_load(sB + (bq * np + bpn) * B_PANEL_BYTES, srcB + (size_t)kc * S * B_PANEL_BYTES, B_PANEL_BYTES,
-                        &full_bar[stage]);
-            }
-            __syncwarp();
             if (++stage == B.stages) { stage = 0; phase ^= 1u; }
           }
         }
       }
     }
-    // wait for every copy this warp issued (bounded) before the CTA may exit
-    if (lane == 0) {
+    // Before the CTA may exit, every issued copy has landed (bounded wait).  A
+    // later copy into a stage is issued only after the previous one was
+    // consumed, so only the latest copy into each stage can still be in flight.
+    prod_bar();
+    if (pw == 0 && lane == 0) {
       for (int s = 0; s < B.stages; ++s) {
-        // the most recent use of stage s had parity phase if s < stage, else phase ^ 1
-        const uint32_t par = (s >= stage) ? (phase ^ 1u) : phase;
+        long long last = -1;
+        for (int q = 0; q < NPROD; ++q) last = max(last, last_seq[q][s]);
+        if (last < 0) continue;
+        const uint32_t par = (uint32_t)((last / B.stages) & 1);
         const uint32_t a = smem_u32(&full_bar[s]);
         for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, par); ++it) {
           if ((it & 255) == 255) __nanosleep(128);
@@ -351,8 +383,9 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp == 1 || warp == MMA_WARP1) {
+    // ------------------------------------------------------------ MMA issuers, one per 128-row half
+    const int mh = warp == 1 ? 0 : 1;
     if (lane == 0) {
       int stage = 0, abuf = 0;
       uint32_t phase = 0, aphase = 0;
@@ -365,7 +398,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const int o = d.o, v = d.v;
       const long long item = gitem - P.item0 + P.item_base;
       (void)v;
-        const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+        int t, chunk;
+        item_slot(d, item, t, chunk);
         const int4 tr = P.w.trip[t];
         const int occ[3] = {tr.x, tr.y, tr.z};
         const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
@@ -389,13 +423,11 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
               const uint32_t sA = smem_u32(sm + stage * STAGE_BYTES);
               const uint64_t bd = sdesc(sA + S * A_SLICE_BYTES);
 #pragma unroll
-              for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int a = 0; a < S; ++a) {
-                  const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + h * (A_SLICE_BYTES / 2));
-                  const uint32_t dcol = dbase + (uint32_t)(h * S * 32 + a * np * NT);
-                  mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > kc0 || a > 0) ? 1u : 0u);
-                }
+              for (int a = 0; a < S; ++a) {
+                const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + mh * (A_SLICE_BYTES / 2));
+                const uint32_t dcol = dbase + (uint32_t)(mh * S * 32 + a * np * NT);
+                mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > kc0 || a > 0) ? 1u : 0u);
+              }
               mma_commit(&empty_bar[stage]);
               if (++stage == B.stages) { stage = 0; phase ^= 1u; }
             }
@@ -407,8 +439,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
         }
       }
       // all MMAs issued by this thread complete before TMEM is released
-      mma_commit(&teardown_bar);
-      const uint32_t a = smem_u32(&teardown_bar);
+      mma_commit(&teardown_bar[mh]);
+      const uint32_t a = smem_u32(&teardown_bar[mh]);
       for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, 0); ++it) {
         if ((it & 255) == 255) __nanosleep(128);
         if (it == WAIT_LIMIT - 1) atomicCAS(B.err, 0, ERR_TIMEOUT_TEARDOWN);
@@ -432,7 +464,8 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       const int o = d.o, v = d.v;
       const long long item = gitem - P.item0 + P.item_base;
       (void)v;
-      const int t = (int)(item / d.items_per_trip), chunk = (int)(item % d.items_per_trip);
+      int t, chunk;
+      const long long islot = item_slot(d, item, t, chunk);
       const int4 tr = P.w.trip[t];
       const int occ[3] = {tr.x, tr.y, tr.z};
       const double eijk = __ldg(P.eps + occ[0]) + __ldg(P.eps + occ[1]) + __ldg(P.eps + occ[2]);
@@ -548,7 +581,7 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
         double tot = 0.0;
 #pragma unroll
         for (int wq = 0; wq < EPI_WARPS; ++wq) tot += red[wq];
-        P.w.partial[item] = tot;
+        P.w.partial[islot] = tot;
       }
       epi_bar();
     }
@@ -635,6 +668,11 @@ int stages_for(int S) {
   const int budget = 227 * 1024 - W_BYTES - 1024 - 256;
   int st = budget / stage_bytes;
   if (st > MAX_STAGES) st = MAX_STAGES;
+  // The producers' parity waits on the empty barriers stay unambiguous only
+  // while a producer can be at most one ring cycle ahead of the stage's last
+  // use, which the in-order MMA consumer guarantees when stages >= NPROD.
+  static_assert((227 * 1024 - W_BYTES - 1024 - 256) / (MAXS * (A_SLICE_BYTES + 2 * B_PANEL_BYTES)) >= NPROD,
+                "fewer pipeline stages than producer warps");
   return st;
 }
 
