@@ -87,11 +87,14 @@ typedef struct {
   int slices;                /* BF16 slices per operand (0 for TC_FP64) */
   int o, v;
   double queue_seconds;      /* serving: time from tc_submit to the start of its GPU work */
-  double kernel_seconds;     /* device time of the fused W/V/energy kernel (CUDA events on the call's stream) */
+  double kernel_seconds;     /* device time of the W/V/energy kernels (CUDA events on the call's stream):
+                                FP64, the fused kernel; split path, all W-term and energy launches */
   double prep_seconds;       /* device time of the slicing / re-layout kernels (split path), else 0 */
-  long long n_items;         /* work items (triplet x tile-orbit chunk) the fused kernel processed */
+  long long n_items;         /* energy work items (triplet x tile-orbit chunk) processed */
   int launches;              /* kernels this call launched */
   int reserved;
+  double wterm_seconds;      /* device time of the kernels that form W: FP64, the fused kernel (= kernel_seconds);
+                                split path, the W-term GEMM launches alone (blocking entry points only) */
 } tc_result;
 
 /* Create a context on opt->device (opt may be NULL: device 0, defaults).

@@ -47,7 +47,6 @@ tc_status check_args(tc_ctx *ctx, int o, int v, const double *eps, const double 
   if (*prec == TC_SPLIT_BF16) {
     if (*slices <= 0) *slices = ctx->default_slices;
     if (*slices < 2 || *slices > 4) return fail(ctx, TC_EINVAL, "slices must be 2, 3 or 4 (got %d)", *slices);
-    if (o > 255) return fail(ctx, TC_EINVAL, "split path supports o <= 255 (got %d)", o);
   } else {
     *slices = 0;
   }
@@ -87,20 +86,39 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   TC_CUDA(ctx, cudaMemsetAsync(w.counter, 0, 2 * sizeof(unsigned), st));
   if (e_ijk_dev) TC_CUDA(ctx, cudaMemsetAsync(e_ijk_dev, 0, sizeof(double) * (size_t)o * o * o, st));
   int launches = 1;                                      // reduce_jobs
+  int nblocks = 0;                                       // split path: blocks of triplets
   if (split) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
-    TC_CUDA(ctx, tc::launch_split_prep(d, slices, in, ctx->ws_split.p, SL, st));
+    TC_CUDA(ctx, tc::launch_split_prep(SL, in, ctx->ws_split.p, st));
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
-    launches += 6;
+    launches += tc::split_prep_launches();
   }
   if (d.n_items > 0) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     if (split) {
-      tc::SplitBatch b{};
-      b.njobs = 1;
-      b.err = w.err;
-      b.job[0] = tc::split_job(d, in, ctx->ws_split.p, SL, w);
-      TC_CUDA(ctx, tc::launch_split(b, slices, ctx->num_sms, st));
+      // blocks of nb triplets: W-term GEMMs into the W-term buffer, then the
+      // energy over the block's orbits
+      const int nb = SL.g.nb;
+      nblocks = (d.n_trip + nb - 1) / nb;
+      while ((int)ctx->wev.size() < 2 * nblocks) {
+        cudaEvent_t e = nullptr;
+        TC_CUDA(ctx, cudaEventCreate(&e));
+        ctx->wev.push_back(e);
+      }
+      static thread_local tc::WtBatch wb;
+      static thread_local tc::EnBatch eb;
+      for (int blk = 0; blk < nblocks; ++blk) {
+        const int t0 = blk * nb, nt = std::min(nb, d.n_trip - t0);
+        wb = tc::WtBatch{};
+        wb.njobs = 1;
+        wb.err = w.err;
+        wb.job[0] = tc::wt_job(SL, ctx->ws_split.p, w.trip, t0, nt);
+        eb = tc::EnBatch{};
+        eb.njobs = 1;
+        eb.job[0] = tc::en_job(d, SL, ctx->ws_split.p, in, w, t0, nt);
+        TC_CUDA(ctx, tc::launch_split_block(wb, eb, slices, ctx->num_sms, st, ctx->wev[2 * blk], ctx->wev[2 * blk + 1]));
+      }
+      launches += 2 * nblocks - 1;
     } else {
       int per_sm = 0;
       TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
@@ -142,6 +160,15 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
     float ms = 0.f;
     TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
     out->kernel_seconds = 1e-3 * ms;
+    out->wterm_seconds = out->kernel_seconds;
+    if (split) {
+      double wsum = 0.0;
+      for (int blk = 0; blk < nblocks; ++blk) {
+        TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->wev[2 * blk], ctx->wev[2 * blk + 1]));
+        wsum += 1e-3 * ms;
+      }
+      out->wterm_seconds = wsum;
+    }
   }
   if (split) {
     float ms = 0.f;
@@ -236,6 +263,7 @@ void tc_finalize(tc_ctx *ctx) {
   ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->wev) if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -4,6 +4,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/tc.h"
 
@@ -43,10 +44,11 @@ struct tc_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   tc::DevBuf ws;                            // tables, partials and sums, reused across calls
-  tc::DevBuf ws_split;                      // BF16 operand images and FP32 copies
+  tc::DevBuf ws_split;                      // BF16 operand images, FP32 copies, W-term buffer
   tc::DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies
   double *host_out = nullptr;               // pinned read-back slot
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};     // kernel timing
+  std::vector<cudaEvent_t> wev;             // split path: a pair around each W-term launch (grown on demand)
   std::mutex serve_mu;                      // guards creation of the serving engine
   tc::Server *server = nullptr;
 };

@@ -35,18 +35,6 @@ struct Dims {
   long long n_items;
 };
 
-// Work item q of a job (its sequence number in launch order) -> (triplet t,
-// orbit chunk c).  Items run chunk-major: the CTAs in flight at one time work
-// on the same few tile triples for many triplets, so the operand tiles they
-// stream are shared through L2.  The item's partial keeps the triplet-major
-// slot t * items_per_trip + c, so the order of the final reduction (and every
-// bit of the result) does not depend on the launch order.
-__host__ __device__ inline long long item_slot(const Dims &d, long long q, int &t, int &chunk) {
-  chunk = (int)(q / d.n_trip);
-  t = (int)(q % d.n_trip);
-  return (long long)t * d.items_per_trip + chunk;
-}
-
 struct Inputs {        // device pointers, layouts as in include/tc.h
   const double *eps, *t1, *t2, *ovvv, *ovoo, *ovov;
 };
@@ -94,40 +82,69 @@ cudaError_t launch_fp64(const FpBatch &b, int grid, cudaStream_t st);
 void fp64_node_params(const FpBatch &b, int grid, void **args, cudaKernelNodeParams *p);
 
 // ---------------------------------------------------------------- split path
-// Byte offsets of the BF16 operand images and FP32 copies inside a job's
-// split workspace.
+// Geometry of one job's split path (tc_split.cu): W-term GEMMs with 128-row M
+// tiles over the v^2 virtual pairs, K blocks of 16, N chunks over v.
+struct SplitGeom {
+  int o, v, S;
+  int mt;                // M tiles: ceil(v^2 / 128)
+  int kbv, kbo;          // K blocks over a virtual / an occupied index
+  int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
+  int ys;                // row stride of a W-term tile in floats (nc + 4)
+  int nb;                // triplets per block (capacity of the W-term buffer)
+};
+// Byte offsets of the operand images, FP32 copies and W-term buffer inside a
+// job's split workspace.
 struct SplitLayout {
-  int vpad, opad;
-  size_t ovvv, t2, t2h, ovoo, t1f, ovovf;
+  SplitGeom g;
+  size_t pa, pa2, hc, hc2, tb, hb, t1f, ovovf, y;
   size_t total;
 };
-struct SplitJob {
-  Dims d;
-  int kch_p, kch_h;      // K blocks (of 16) of particle / hole products
-  int T;                 // virtual tiles
-  const unsigned char *imgA_p, *imgA_h, *imgB_p, *imgB_h;   // operand images
-  const float *t1f, *ovovf;
-  const double *eps;
-  Work w;
-  long long item0;       // first global item of this job in the launch
-  long long item_base;   // the job's own index of that item
-  long long n_run;       // items of this job in the launch (0: all n_items)
+struct WtJob {           // one job's block of triplets in a W-term launch
+  SplitGeom g;
+  const int4 *trip;      // the job's triplet table
+  int t0, nt;            // triplets [t0, t0 + nt) of the table
+  const unsigned char *pa, *pa2, *hc, *hc2, *tb, *hb;
+  float *y;              // W-term buffer [nt][3][nch][mt * 128][ys]
+  long long item0;       // first global item of this job in the launch (set by the launcher)
 };
-struct SplitBatch {
+struct WtBatch {
   int njobs;
-  int stages;            // set by launch_split
+  int stages, nprod;     // set by the launcher
+  size_t slot, sum_off;  // set by the launcher: stage stride and tile-sum offset in shared memory
   long long total_items;
   int *err;
-  SplitJob job[MAX_BATCH];
+  WtJob job[MAX_BATCH];
+};
+struct EnJob {           // one job's block of triplets in an energy launch
+  Dims d;
+  SplitGeom g;
+  const int4 *trip, *orb;
+  const double *eps;
+  const float *t1f, *ovovf, *y;
+  double *partial;       // [n_items], slot t * items_per_trip + chunk
+  int t0, nt;
+  long long item0;
+};
+struct EnBatch {
+  int njobs;
+  long long total_items;
+  EnJob job[MAX_BATCH];
 };
 int split_tile();
+SplitGeom split_geom(int o, int v, int S);
 SplitLayout split_layout(int o, int v, int S);
-cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st);
-SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitLayout &L, const Work &w);
-cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st);
-// Prepare b (item offsets, stages) and fill kernel-node parameters of the launch
-// launch_split would make; also performs launch_split's one-time set-up.
-cudaError_t split_node_params(SplitBatch &b, int S, int grid, void **args, cudaKernelNodeParams *p, cudaStream_t st);
+cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st);
+int split_prep_launches();
+WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt);
+EnJob en_job(const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w, int t0, int nt);
+// One block of triplets: the W-term launch, then the energy launch, on st.
+// w0 / w1 (optional) are recorded around the W-term launch.
+cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cudaStream_t st,
+                               cudaEvent_t w0 = nullptr, cudaEvent_t w1 = nullptr);
+// Prepare both batches as launch_split_block would and fill kernel-node
+// parameters of its two launches; wargs[0] / eargs[0] point to wb / eb.
+cudaError_t split_block_params(WtBatch &wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
+                               cudaKernelNodeParams *wp, cudaKernelNodeParams *ep);
 
 // ---------------------------------------------------------------- reduction
 struct RedJob {

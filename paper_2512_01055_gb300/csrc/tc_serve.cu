@@ -55,8 +55,9 @@ struct Req {
   cudaStream_t st = nullptr;
   cudaEvent_t ready = nullptr;
   bool waited = false;                    // the compute stream waits on `ready` once
-  long long next_item = 0;
-  double cost_per_item = 1.0;
+  long long units = 0;                    // work units: FP64 items, or split-path triplets
+  long long next_item = 0;                // next unit to run
+  double cost_per_item = 1.0;             // cost of one unit
   St state = St::Queued;
   tc_status status = TC_OK;
   tc_result res{};
@@ -92,6 +93,7 @@ struct Server {
   cudaGraph_t graph[N_GROUPS] = {};
   cudaGraphExec_t exec[N_GROUPS] = {};
   cudaGraphNode_t knode[N_GROUPS] = {};
+  cudaGraphNode_t enode[N_GROUPS] = {};   // split groups: the energy launch after the W-term launch
   double rate[N_GROUPS] = {3e7, 4e8, 3e8, 2e8};   // cost units per second (refined as iterations run)
   int rr = 0;                             // round-robin cursor over groups
   int fault_alloc = 0, fault_stall_ms = 0;
@@ -186,7 +188,7 @@ void Server::start_prep(const std::shared_ptr<Req> &r) {
   cudaMemsetAsync(q.w.counter, 0, 2 * sizeof(unsigned), q.st);
   if (split) {
     const Inputs in{q.din[0], q.din[1], q.din[2], q.din[3], q.din[4], q.din[5]};
-    launch_split_prep(q.d, q.slices, in, q.mem + q.off_split, q.SL, q.st);
+    launch_split_prep(q.SL, in, q.mem + q.off_split, q.st);
   }
   cudaEventRecord(q.ready, q.st);
   e = cudaStreamSynchronize(q.st);        // the copies read the job's host vectors
@@ -245,12 +247,14 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     std::vector<int> still;
     for (int j : open) {
       Req &q = *jobs[j];
-      const long long rem = q.d.n_items - q.next_item - take[j];
+      // split jobs run at most one block of triplets (the W-term buffer) per launch
+      const long long cap = g == 0 ? q.units : q.SL.g.nb;
+      const long long rem = std::min(q.units - q.next_item, cap) - take[j];
       const long long want = std::max<long long>(1, (long long)(share / q.cost_per_item));
       const long long t = std::min(rem, want);
       take[j] += t;
       budget -= t * q.cost_per_item;
-      if (q.d.n_items - q.next_item - take[j] > 0 && t == want) still.push_back(j);
+      if (rem - t > 0 && t == want) still.push_back(j);
     }
     if (still.size() == open.size() && budget <= 0) break;
     open.swap(still);
@@ -260,10 +264,11 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     if (!q.waited) { cudaStreamWaitEvent(compute, q.ready, 0); q.waited = true; }
     if (!q.started) { q.started = true; q.t_start = Clock::now(); }
   }
-  void *args[1];
-  cudaKernelNodeParams kp{};
+  void *args[1], *eargs[1];
+  cudaKernelNodeParams kp{}, ep{};
   static thread_local FpBatch fb;
-  static thread_local SplitBatch sb;
+  static thread_local WtBatch wb;
+  static thread_local EnBatch eb;
   long long total = 0;
   double cost = 0;
   cudaError_t e = cudaSuccess;
@@ -282,20 +287,20 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     const long long grid = std::min<long long>((long long)ctx->num_sms * fp64_per_sm, total);
     fp64_node_params(fb, (int)grid, args, &kp);
   } else {
-    sb = SplitBatch{};
-    sb.njobs = nj;
-    sb.err = d_err;
+    wb = WtBatch{};
+    eb = EnBatch{};
+    wb.njobs = eb.njobs = nj;
+    wb.err = d_err;
     for (int j = 0; j < nj; ++j) {
       Req &q = *jobs[j];
       const Inputs in{q.din[0], q.din[1], q.din[2], q.din[3], q.din[4], q.din[5]};
-      sb.job[j] = split_job(q.d, in, q.mem + q.off_split, q.SL, q.w);
-      sb.job[j].item_base = q.next_item;
-      sb.job[j].n_run = take[j];
+      const int t0 = (int)q.next_item, nt = (int)take[j];
+      wb.job[j] = wt_job(q.SL, q.mem + q.off_split, q.w.trip, t0, nt);
+      eb.job[j] = en_job(q.d, q.SL, q.mem + q.off_split, in, q.w, t0, nt);
       total += take[j];
       cost += take[j] * q.cost_per_item;
     }
-    const long long grid = std::min<long long>(ctx->num_sms, total);
-    e = split_node_params(sb, g + 1, (int)grid, args, &kp, compute);
+    e = split_block_params(wb, eb, g + 1, ctx->num_sms, args, eargs, &kp, &ep);
   }
   if (e != cudaSuccess) return false;
   if (!exec[g]) {
@@ -312,9 +317,11 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
       e = cudaGraphAddMemsetNode(&mnode, graph[g], nullptr, 0, &mp);
     }
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&knode[g], graph[g], mnode ? &mnode : nullptr, mnode ? 1 : 0, &kp);
+    if (e == cudaSuccess && g != 0) e = cudaGraphAddKernelNode(&enode[g], graph[g], &knode[g], 1, &ep);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec[g], graph[g], 0);
   } else {
     e = cudaGraphExecKernelNodeSetParams(exec[g], knode[g], &kp);
+    if (e == cudaSuccess && g != 0) e = cudaGraphExecKernelNodeSetParams(exec[g], enode[g], &ep);
   }
   const auto t0 = Clock::now();
   if (e == cudaSuccess) e = cudaGraphLaunch(exec[g], compute);
@@ -402,14 +409,14 @@ void Server::sched_loop() {
     for (int k = 0; k < N_GROUPS && g < 0; ++k) {
       const int gg = (rr + k) % N_GROUPS;
       for (auto &r : active)
-        if (r->group == gg && r->state == St::Ready && r->next_item < r->d.n_items && (int)jobs.size() < MAX_BATCH)
+        if (r->group == gg && r->state == St::Ready && r->next_item < r->units && (int)jobs.size() < MAX_BATCH)
           jobs.push_back(r);
       if (!jobs.empty()) g = gg;
     }
     // jobs with no items at all (o = 1 or v too small to matter) complete directly
     std::vector<std::shared_ptr<Req>> done;
     for (auto &r : active)
-      if (r->state == St::Ready && r->next_item >= r->d.n_items) { done.push_back(r); r->state = St::Prep; }
+      if (r->state == St::Ready && r->next_item >= r->units) { done.push_back(r); r->state = St::Prep; }
     if (g < 0 && done.empty()) {
       cv_sched.wait_for(lk, std::chrono::milliseconds(2));
       continue;
@@ -419,7 +426,7 @@ void Server::sched_loop() {
     if (g >= 0) {
       run_iteration(g, jobs);
       for (auto &r : jobs)
-        if (r->state == St::Ready && r->next_item >= r->d.n_items) { done.push_back(r); r->state = St::Prep; }
+        if (r->state == St::Ready && r->next_item >= r->units) { done.push_back(r); r->state = St::Prep; }
     }
     if (!done.empty()) {
       for (auto &r : done)
@@ -489,7 +496,7 @@ tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket) {
   if (o <= 0 || v <= 0 || (long long)o * v * v * v > (1LL << 40)) return TC_EINVAL;
   if (!job->eps || !job->t1 || !job->t2 || !job->ints.ovvv || !job->ints.ovoo || !job->ints.ovov) return TC_EINVAL;
   if (prec != TC_FP64 && prec != TC_SPLIT_BF16) return TC_EINVAL;
-  if (prec == TC_SPLIT_BF16 && (slices < 2 || slices > 4 || o > 255)) return TC_EINVAL;
+  if (prec == TC_SPLIT_BF16 && (slices < 2 || slices > 4)) return TC_EINVAL;
   if (prec == TC_FP64) slices = 0;
   tc::Server *s = nullptr;
   tc_status st = get_server(ctx, &s);
@@ -506,7 +513,9 @@ tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket) {
   r->L = tc::plan::make_layout(r->d);
   if (split) r->SL = tc::split_layout(o, v, slices);
   r->footprint = (r->dev_inputs ? 0 : tc::plan::align256(tc::plan::input_bytes(o, v))) + r->L.total + r->SL.total;
-  r->cost_per_item = (double)r->d.orb_per_item * (v + 16.0 * ((o + 15) / 16));
+  // cost units: one orbit's worth of K values; a split unit is a whole triplet
+  r->units = split ? r->d.n_trip : r->d.n_items;
+  r->cost_per_item = (double)(split ? r->d.n_orb : r->d.orb_per_item) * (v + 16.0 * ((o + 15) / 16));
   if (r->footprint > ctx->budget) return TC_ENOMEM;
   const double *src[6] = {job->eps, job->t1, job->t2, job->ints.ovvv, job->ints.ovoo, job->ints.ovov};
   const size_t O = o, V = v;

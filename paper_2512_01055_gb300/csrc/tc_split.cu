@@ -1,109 +1,88 @@
 // Split-precision path: W (Eqs. 2, 5) from BF16 slices on the tcgen05 tensor
-// cores (FP32 accumulation in TMEM), V (Eq. 3) in FP32, D (Fig. 4 sign) and
-// its reciprocal in FP64, per-item energy sums in FP64.
+// cores (FP32 accumulation in TMEM), V (Eq. 3) in FP32, D (Fig. 4 sign) in FP64
+// with an FP32 reciprocal, energy terms summed in FP32 over rows of 16 points
+// and in FP64 beyond.
 //
 // Slices.  Every FP64 operand x is written as s BF16 numbers x_0 + ... + x_{s-1}
 // with x_0 = bf16(x) and x_p = bf16(x - x_0 - ... - x_{p-1}) (round to
 // nearest; the FP64 residual is exact), the splitting used to emulate higher
-// precision with BF16 products (Henry, Tang, Heinecke, ARITH 2019; an
-// Ozaki-style error-free-ish expansion with per-element exponents).  A product
-// is approximated by the slice pairs with p + q < s, grouped by level L = p + q.
+// precision with BF16 products (Henry, Tang, Heinecke, ARITH 2019).  A product
+// is approximated by the slice pairs (p, q) with p + q < s.
 //
-// GEMM tiles.  Virtual tiles have edge 16.  A "job" is one A tile of 256 rows
-// (pairs of two virtual tiles) and one or two B panels of 16 rows:
-//   particle:  A = (x a | b f) = ovvv[x][a][b][f],  B = t2[y][z][c][f],  K = v
-//   hole:      A = t2[l][z][a][b] (re-laid out with l last),  B = -(x c | y l),  K = o
-// For each K step of 16 the MMA warp issues, per 128-row half, one MMA per A
-// slice p with the B slices 0 .. s-1-p stacked along N, so each A slice is read
-// from shared memory once and lands in its level's TMEM columns.  The drain
-// warps add the levels (smallest first) and scatter the 256 x 16 (x panels)
-// results into the orbit's W blocks in shared memory with the job's index
-// permutation.  After all jobs of an orbit, the same warps evaluate the Eq. 1
-// bracket over the orbit's canonical points (as in the FP64 path) and
-// accumulate FP64 partials.
+// W as three GEMMs per triplet.  For one occupied triplet (i, j, k), the six
+// terms X of Eq. 5 regroup by the virtual index that the t2 factor of the
+// particle product (and the integral of the hole product) carries:
+//   W_abc = F(i,j,k)[ab, c] + F(i,k,j)[ac, b] + F(j,k,i)[bc, a]
+//   F(p,q,r)[xy, z] =   sum_f G_pf^xy t_rq^zf + sum_f G_qf^yx t_rp^zf
+//                     - sum_l t_lp^yx G_rq^zl - sum_l t_lq^xy G_rp^zl
+// (G_pq^rs = (pr|qs)).  F(i,j,k) holds the particle parts of X(ijk,abc) and
+// X(jik,bac) and the hole parts of X(kji,cba) and X(kij,cab); F(i,k,j) and
+// F(j,k,i) hold the other four pairs.  Each F is one GEMM with M = v^2 row
+// pairs (x, y), N = v and K = 2v + 2o (four segments), so the tensor cores run
+// with N up to 224 instead of the 16-wide panels a tile-local W would allow.
 //
-// Operand images.  The slicer writes every A tile (256 rows x 16 K) and B
-// panel (16 rows x 16 K) of every K block directly in the tensor core's
-// K-major no-swizzle layout (8-row x 16-byte core matrices, the two K halves
-// 128 bytes apart, 8-row groups 256 bytes apart), tile-major with the S slices
-// of a block contiguous.  One pipeline stage is then one contiguous bulk copy
-// (cp.async.bulk) for A and one per B slice, instead of hundreds of 32-byte
-// tensor-map rows per stage.
+// W-term kernel.  A work item is (128-row M tile, triplet, F, N chunk); items
+// run M-tile-major so the triplets of one launch share A tiles through L2.
+// Per K block of 16 the MMA warp issues one MMA per slice pair: level 0 into
+// accumulator L0, levels >= 1 into L1 (TMEM columns [0, nc) and [nc, 2nc)).
+// The FP32 accumulation along K rounds systematically, so L0 is restarted
+// every KCHAIN blocks (256 K values): the drain warps copy each finished chain
+// out of TMEM and add it into the tile's FP32 sum in shared memory; the last
+// chain also brings L1.  A finished tile leaves with one bulk store into the
+// job's W-term buffer Y[triplet][F][chunk][row][z].
 //
-// Warp roles (320 threads): warp 0 issues the bulk copies, warp 1 owns TMEM
-// and lane 0 issues MMAs, warps 2-9 (two warpgroups, one per 128-row half of
-// each job) drain TMEM and run the energy epilogue.
+// Energy kernel.  A work item is (triplet, chunk of tile orbits) as in the
+// FP64 path.  Per orbit it assembles the six 16^3 W blocks from the three F
+// buffers in shared memory and evaluates the Eq. 1 bracket at the orbit's
+// canonical points, writing one FP64 partial per item.
+//
+// Operand images.  The slicer writes every operand block of 16 K values
+// directly in the tensor core's K-major no-swizzle layout (8-row x 16-byte
+// core matrices, the two K halves 128 bytes apart, 8-row groups 256 bytes
+// apart), with the s slices of a block contiguous, so a pipeline stage is two
+// contiguous bulk copies (cp.async.bulk): the A block and the B block.
+//
+// Warp roles of the W-term kernel (384 threads): warps 0, 10 and 11 issue the
+// bulk copies (a warp completes about one stage per ~0.37 us, several warps
+// overlap), warp 1 owns TMEM and lane 0 issues the MMAs, warps 2-9 drain TMEM
+// (warp w reads TMEM lanes 32 (w % 4) .. +31, half the columns each).
 // Every mbarrier wait is bounded; on expiry the kernel records an error code,
 // lets every role leave its loop, waits (bounded) for its own copies and MMAs
 // and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
-#include <mutex>
+#include <algorithm>
 
 #include "tc_internal.cuh"
 
 namespace tc {
 namespace {
 
-constexpr int NT = 16;                    // virtual tile edge
-constexpr int KC = 16;                    // K per pipeline stage (32-byte rows, 32B swizzle)
-constexpr int A_SLICE_BYTES = 256 * KC * 2;
-constexpr int B_PANEL_BYTES = NT * KC * 2;
+constexpr int NT = 16;                    // virtual tile edge of the energy orbits
+constexpr int KB = 16;                    // K values per block (one MMA)
+constexpr int MROWS = 128;                // rows of an M tile
+constexpr int A_BLK = MROWS * KB * 2;     // bytes of one A slice block
+constexpr int NCMAX = 224;                // widest N chunk
 constexpr int MAXS = 4;
 constexpr int MAX_STAGES = 8;
-// Copy issue: one warp completes about one pipeline stage per ~0.36 us however
-// many stages it has in flight, while several issuing warps overlap.  NPROD
-// producer warps (warp 0 and warps 10, 11, ...) therefore fill the stages
-// round-robin.
-// MMA issue: one issuing thread spends ~210 ns on the six MMAs of a K block
-// (N = 96, 64, 32 per half); two issuing warps, one per 128-row half of the A
-// tile, bring it to ~150 ns.  Warp 1 issues half 0 and warp 12 half 1.
 constexpr int NPROD = 3;
-constexpr int MMA_WARP1 = 10 + (NPROD - 1);
-constexpr int THREADS = 32 * (MMA_WARP1 + 1);
-constexpr int EPI_THREADS = 256;
-constexpr int EPI_WARPS = EPI_THREADS / 32;
-constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
-constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
-constexpr int W_BYTES = 6 * WBLK * 4;
-constexpr int MAX_JOBS = 72;
+constexpr int THREADS = 384;
+constexpr int DRAIN_THREADS = 256;
+constexpr int MAXG = (NCMAX / 16 + 1) / 2;   // 16-column groups a drain thread holds
+constexpr int SMEM_DYN_MAX = 232448 - 2048;  // opt-in limit minus static shared memory and slack
 constexpr long long WAIT_LIMIT = 1LL << 26;
-// Longest run of K blocks accumulated in one tensor-core accumulator.  The FP32
-// accumulation along K rounds systematically, so longer products are split into
-// chains of at most KCHAIN blocks (256 K values), each drained and added into W.
+// Longest run of K blocks accumulated in one tensor-core accumulator (see above).
 constexpr int KCHAIN = 16;
 
 constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL = 13,
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
 
-// One GEMM job of an (occupied pattern, tile pattern) template.  Every field
-// is a position (0, 1, 2) into the triplet's occupied indices occ[] or the
-// orbit's tile indices tl[], so one template serves every triplet and orbit
-// with the same equality pattern (i > j > k, i = j > k, i > j = k) x
-// (P > Q > R, P = Q > R, P > Q = R, P = Q = R).
-struct TJob {
-  uint8_t kind;              // 0 particle, 1 hole
-  uint8_t np;                // panels (1 or 2)
-  uint8_t apos;              // A tile occupied index: occ[apos]
-  uint8_t tapos, tbpos;      // A rows (a, b): a in tile tl[tapos], b in tile tl[tbpos]
-  uint8_t pad;
-  uint8_t ptpos[2];          // panel tile tl[ptpos]
-  uint8_t p0pos[2];          // particle: y of t2[y][z]; hole: x of (x c|y l)
-  uint8_t p1pos[2];          // particle: z;              hole: y
-  uint8_t blk[2];            // W block (distinct permutation index of the orbit)
-  uint8_t hi[2], lo[2], col[2];   // W positions receiving row/16, row%16 and the panel column
-};
-constexpr int N_PATTERNS = 12;
-__constant__ TJob c_tjobs[N_PATTERNS][MAX_JOBS];
-__constant__ int c_ntjobs[N_PATTERNS];
-
-__host__ __device__ __forceinline__ int pattern_id(const int occ[3], const int tl[3]) {
-  const int op = (occ[0] == occ[1]) ? 1 : ((occ[1] == occ[2]) ? 2 : 0);
-  const int tp = (tl[0] == tl[1] && tl[1] == tl[2]) ? 3 : ((tl[0] == tl[1]) ? 1 : ((tl[1] == tl[2]) ? 2 : 0));
-  return op * 4 + tp;
-}
-
+// energy kernel
+constexpr int EN_THREADS = 256;
+constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
+constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
+constexpr int EN_SMEM = 6 * WBLK * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -143,6 +122,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               :: "l"(gdst), "r"(smem_u32(ssrc)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows
 // x 16 bytes, the next core matrix along K 128 bytes on, the next 8-row group
@@ -177,8 +163,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EPI_THREADS) : "memory"); }
+__device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, %0;" :: "n"(DRAIN_THREADS) : "memory"); }
 __device__ __forceinline__ void prod_bar() { asm volatile("bar.sync 2, %0;" :: "n"(NPROD * 32) : "memory"); }
 
 // Distinct tile block holding each formal permutation of the orbit's tile triple.
@@ -193,87 +180,80 @@ __host__ __device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6
   }
 }
 
-// The GEMM jobs of one (triplet, orbit) pattern: for every distinct block s and
-// every permutation u of Eq. 5, one particle and one hole product; products
-// that share an A tile are paired into one job (at most two panels).  Built on
-// the host from representative index values; positions are stored.
-int host_build_template(const int occ[3], const int tl[3], TJob *jobs) {
-  auto opos = [&](int val) { return val == occ[0] ? 0 : (val == occ[1] ? 1 : 2); };
-  auto tpos = [&](int val) { return val == tl[0] ? 0 : (val == tl[1] ? 1 : 2); };
-  int blk[6];
-  orbit_blocks(tl, blk);
-  int n = 0;
-  for (int kind = 0; kind < 2; ++kind) {
-    const int first = n;
-    for (int s = 0; s < 6; ++s) {
-      if (blk[s] != s) continue;
-      int T[3];
-      for (int p = 0; p < 3; ++p) T[p] = tl[perm3(s, p)];
-      for (int u = 0; u < 6; ++u) {
-        const int u0 = perm3(u, 0), u1 = perm3(u, 1), u2 = perm3(u, 2);
-        int aocc, ta, tb, ptile, po0, po1, hi, lo, col;
-        if (kind == 0) {   // sum_f (x p | q f) t2[z][y][r][f]: rows (u0, u1), column u2
-          aocc = occ[u0]; ta = T[u0]; tb = T[u1];
-          ptile = T[u2]; po0 = occ[u2]; po1 = occ[u1];
-          hi = u0; lo = u1; col = u2;
-        } else {           // -sum_l (x p | y l) t2[l][z][q][r]: rows (u1, u2), column u0
-          aocc = occ[u2]; ta = T[u1]; tb = T[u2];
-          ptile = T[u0]; po0 = occ[u0]; po1 = occ[u1];
-          hi = u1; lo = u2; col = u0;
-        }
-        int j = -1;
-        for (int q = first; q < n; ++q)
-          if (jobs[q].np == 1 && occ[jobs[q].apos] == aocc && tl[jobs[q].tapos] == ta && tl[jobs[q].tbpos] == tb) {
-            j = q;
-            break;
-          }
-        int slot = 1;
-        if (j < 0) {
-          j = n++;
-          jobs[j] = TJob{};
-          jobs[j].kind = (uint8_t)kind;
-          jobs[j].apos = (uint8_t)opos(aocc);
-          jobs[j].tapos = (uint8_t)tpos(ta);
-          jobs[j].tbpos = (uint8_t)tpos(tb);
-          slot = 0;
-        }
-        jobs[j].np = (uint8_t)(slot + 1);
-        jobs[j].ptpos[slot] = (uint8_t)tpos(ptile);
-        jobs[j].p0pos[slot] = (uint8_t)opos(po0);
-        jobs[j].p1pos[slot] = (uint8_t)opos(po1);
-        jobs[j].blk[slot] = (uint8_t)s;
-        jobs[j].hi[slot] = (uint8_t)hi; jobs[j].lo[slot] = (uint8_t)lo; jobs[j].col[slot] = (uint8_t)col;
-      }
-    }
+// ---------------------------------------------------------------- W-term kernel
+
+// Item q of a job -> (M tile, triplet in the block, F, N chunk), M-tile-major.
+__device__ __forceinline__ void wt_decode(const WtJob &J, long long q, int &m, int &tl, int &g, int &nci) {
+  nci = (int)(q % J.g.nch);
+  q /= J.g.nch;
+  g = (int)(q % 3);
+  q /= 3;
+  tl = (int)(q % J.nt);
+  m = (int)(q / J.nt);
+}
+
+// Occupied indices (p, q, r) of F number g for triplet (i, j, k):
+// F(i,j,k), F(i,k,j), F(j,k,i).
+__device__ __forceinline__ void wt_occ(const WtJob &J, int tl, int g, int &p, int &q, int &r) {
+  const int4 t = J.trip[J.t0 + tl];
+  if (g == 0)      { p = t.x; q = t.y; r = t.z; }
+  else if (g == 1) { p = t.x; q = t.z; r = t.y; }
+  else             { p = t.y; q = t.z; r = t.x; }
+}
+
+// Sources of K block kc of an item: A block (S slices of 128 x 16) and B block
+// (S slices of nc x 16).  Segments: particle G_p/t_rq, particle G_q/t_rp, hole
+// t_.p/G_rq, hole t_.q/G_rp.
+template <int S>
+__device__ __forceinline__ void wt_src(const WtJob &J, int m, int nci, int p, int q, int r, int kc,
+                                       const unsigned char *&a, const unsigned char *&b) {
+  const SplitGeom &G = J.g;
+  const size_t ablk = (size_t)S * A_BLK, bblk = (size_t)S * G.nc * 32;
+  int kb = kc;
+  if (kb < G.kbv) {
+    a = J.pa + (((size_t)p * G.mt + m) * G.kbv + kb) * ablk;
+    b = J.tb + ((((size_t)r * G.o + q) * G.nch + nci) * G.kbv + kb) * bblk;
+    return;
   }
-  return n;
+  kb -= G.kbv;
+  if (kb < G.kbv) {
+    a = J.pa2 + (((size_t)q * G.mt + m) * G.kbv + kb) * ablk;
+    b = J.tb + ((((size_t)r * G.o + p) * G.nch + nci) * G.kbv + kb) * bblk;
+    return;
+  }
+  kb -= G.kbv;
+  if (kb < G.kbo) {
+    a = J.hc2 + (((size_t)p * G.mt + m) * G.kbo + kb) * ablk;
+    b = J.hb + ((((size_t)r * G.o + q) * G.nch + nci) * G.kbo + kb) * bblk;
+    return;
+  }
+  kb -= G.kbo;
+  a = J.hc + (((size_t)q * G.mt + m) * G.kbo + kb) * ablk;
+  b = J.hb + ((((size_t)r * G.o + p) * G.nch + nci) * G.kbo + kb) * bblk;
 }
 
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
-tc_split_kernel(const __grid_constant__ SplitBatch B) {
+tc_wterm_kernel(const __grid_constant__ WtBatch B) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int STAGE_BYTES = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
-  float *Wsm = (float *)(sm + B.stages * STAGE_BYTES);
+  float *sum = (float *)(sm + B.sum_off);       // the tile's FP32 sum [128][ys]
 
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
-  __shared__ __align__(8) uint64_t accfull_bar[2], accempty_bar[2], teardown_bar[2];
+  __shared__ __align__(8) uint64_t accfull_bar, accempty_bar, teardown_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
-  __shared__ int epi_ok;
-  __shared__ double red[EPI_WARPS];
+  __shared__ int drain_ok;
   __shared__ long long last_seq[NPROD][MAX_STAGES];   // per producer: its latest copy into each stage
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid < NPROD * MAX_STAGES) last_seq[tid / MAX_STAGES][tid % MAX_STAGES] = -1;
   if (tid == 0) {
-    // a stage is free, and an accumulator buffer full, once both MMA warps committed
-    for (int s = 0; s < B.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 2); }
-    for (int b = 0; b < 2; ++b) { mbar_init(&accfull_bar[b], 2); mbar_init(&accempty_bar[b], 1); }
-    mbar_init(&teardown_bar[0], 1);
-    mbar_init(&teardown_bar[1], 1);
+    for (int s = 0; s < B.stages; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+    mbar_init(&accfull_bar, 1);
+    mbar_init(&accempty_bar, 1);
+    mbar_init(&teardown_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -282,86 +262,52 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
                  :: "r"(smem_u32(&tmem_base_sh)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (warp >= 2 && warp < 10) {
-    for (int e = tid - 64; e < 6 * WBLK; e += EPI_THREADS) Wsm[e] = 0.f;
-  }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_base_sh;
-  constexpr int BUFCOLS = 2 * S * 32;
 
-  if (warp == 0 || (warp >= 10 && warp < MMA_WARP1)) {
-    // ------------------------------------------------------------ bulk-copy producers (whole warps)
-    // Every producer walks the same sequence of K blocks; producer pw fills the
-    // blocks whose sequence number is pw modulo NPROD.
+  if (warp == 0 || warp >= 10) {
+    // ------------------------------------------------------------ bulk-copy producers
+    // Every active producer walks the same sequence of K blocks; producer pw
+    // fills the blocks whose sequence number is pw modulo nprod.
     const int pw = warp == 0 ? 0 : warp - 9;
-    int stage = 0;
-    uint32_t phase = 0;
-    long long seq = 0;
-    int rr = 0;                               // seq modulo NPROD
-    bool ok = true;
-    int jc = 0;
-    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
-      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
-      const SplitJob &P = B.job[jc];
-      const Dims &d = P.d;
-      const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0 + P.item_base;
-      (void)v;
-      int t, chunk;
-      item_slot(d, item, t, chunk);
-      const int4 tr = P.w.trip[t];
-      const int occ[3] = {tr.x, tr.y, tr.z};
-      const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
-      for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
-        const int4 og = P.w.orb[ob];
-        const int tl[3] = {og.x, og.y, og.z};
-        const int pid = pattern_id(occ, tl);
-        const int nj = c_ntjobs[pid];
-        for (int jb = 0; ok && jb < nj; ++jb) {
-          const TJob J = c_tjobs[pid][jb];
-          const int np = J.np;
-          const int nk = J.kind == 0 ? P.kch_p : P.kch_h;
-          const uint32_t bytes = (uint32_t)S * (A_SLICE_BYTES + np * B_PANEL_BYTES);
-          const int aocc = occ[J.apos], ta = tl[J.tapos], tb = tl[J.tbpos];
-          const int T = P.T;
-          // A image of K block kc: ((aocc*T + ta)*T + tb)*nk + kc, S slices of 8 KB each
-          const unsigned char *srcA = (J.kind == 0 ? P.imgA_p : P.imgA_h) +
-                                      ((size_t)((aocc * T + ta) * T + tb) * nk) * S * A_SLICE_BYTES;
-          // lane 1 + (q * 2 + pn) copies B slice q of panel pn
-          const int bl = lane - 1, bq = bl / 2, bpn = bl % 2;
-          const bool bload = lane >= 1 && bq < S && bpn < np;
-          const unsigned char *srcB = nullptr;
-          if (bload) {
-            const int bt = tl[J.ptpos[bpn]], b0 = occ[J.p0pos[bpn]], b1 = occ[J.p1pos[bpn]];
-            srcB = (J.kind == 0 ? P.imgB_p : P.imgB_h) + ((size_t)((b0 * o + b1) * T + bt) * nk * S + bq) * B_PANEL_BYTES;
-          }
-          for (int kc = 0; kc < nk; ++kc, ++seq) {
-            const bool mine = rr == pw;
-            if (++rr == NPROD) rr = 0;
-            if (mine) {
-              int got = 1;
-              if (lane == 0) {
-                got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
-                if (got) {
-                  last_seq[pw][stage] = seq;
-                  mbar_expect_tx(&full_bar[stage], bytes);
-                }
+    if (pw < B.nprod) {
+      int stage = 0, rr = 0, jc = 0;
+      uint32_t phase = 0;
+      long long seq = 0;
+      bool ok = true;
+      for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
+        while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
+        const WtJob &J = B.job[jc];
+        int m, tl, g, nci, p, q, r;
+        wt_decode(J, gi - J.item0, m, tl, g, nci);
+        wt_occ(J, tl, g, p, q, r);
+        const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
+        const uint32_t abytes = (uint32_t)S * A_BLK, bbytes = (uint32_t)S * J.g.nc * 32;
+        for (int kc = 0; kc < nkb; ++kc, ++seq) {
+          const bool mine = rr == pw;
+          if (++rr == B.nprod) rr = 0;
+          if (mine) {
+            int got = 1;
+            if (lane == 0) {
+              got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
+              if (got) {
+                last_seq[pw][stage] = seq;
+                mbar_expect_tx(&full_bar[stage], abytes + bbytes);
               }
-              got = __shfl_sync(0xffffffffu, got, 0);
-              if (!got) { ok = false; break; }
-              unsigned char *sA = sm + stage * STAGE_BYTES;
-              unsigned char *sB = sA + S * A_SLICE_BYTES;
-              if (lane == 0) {
-                bulk_load(sA, srcA + (size_t)kc * S * A_SLICE_BYTES, S * A_SLICE_BYTES, &full_bar[stage]);
-              } else if (bload) {
-                bulk_load(sB + (bq * np + bpn) * B_PANEL_BYTES, srcB + (size_t)kc * S * B_PANEL_BYTES, B_PANEL_BYTES,
-                          &full_bar[stage]);
-              }
-              __syncwarp();
             }
-            if (++stage == B.stages) { stage = 0; phase ^= 1u; }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) { ok = false; break; }
+            if (lane < 2) {
+              const unsigned char *a, *b;
+              wt_src<S>(J, m, nci, p, q, r, kc, a, b);
+              unsigned char *sA = sm + (size_t)stage * B.slot;
+              if (lane == 0) bulk_load(sA, a, abytes, &full_bar[stage]);
+              else           bulk_load(sA + S * A_BLK, b, bbytes, &full_bar[stage]);
+            }
+            __syncwarp();
           }
+          if (++stage == B.stages) { stage = 0; phase ^= 1u; }
         }
       }
     }
@@ -383,64 +329,60 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
       }
     }
     __syncwarp();
-  } else if (warp == 1 || warp == MMA_WARP1) {
-    // ------------------------------------------------------------ MMA issuers, one per 128-row half
-    const int mh = warp == 1 ? 0 : 1;
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int stage = 0, abuf = 0;
+      int stage = 0, jc = 0;
       uint32_t phase = 0, aphase = 0;
       bool ok = true;
-      int jc = 0;
-    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
-      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
-      const SplitJob &P = B.job[jc];
-      const Dims &d = P.d;
-      const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0 + P.item_base;
-      (void)v;
-        int t, chunk;
-        item_slot(d, item, t, chunk);
-        const int4 tr = P.w.trip[t];
-        const int occ[3] = {tr.x, tr.y, tr.z};
-        const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
-        for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
-          const int4 og = P.w.orb[ob];
-          const int tl[3] = {og.x, og.y, og.z};
-          const int pid = pattern_id(occ, tl);
-          const int nj = c_ntjobs[pid];
-          for (int jb = 0; ok && jb < nj; ++jb) {
-            const int np = c_tjobs[pid][jb].np;
-            const int nk = c_tjobs[pid][jb].kind == 0 ? P.kch_p : P.kch_h;
-            const int nchain = (nk + KCHAIN - 1) / KCHAIN;
-            for (int ch = 0; ok && ch < nchain; ++ch) {
-            const int kc0 = ch * nk / nchain, kc1 = (ch + 1) * nk / nchain;
-            if (!mbar_wait(&accempty_bar[abuf], aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
+      for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
+        while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
+        const WtJob &J = B.job[jc];
+        const int nc = J.g.nc;
+        const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
+        const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
+        const uint32_t id = idesc(128, nc);
+        const uint32_t bslice = (uint32_t)nc * 32;
+        for (int ch = 0; ok && ch < nchain; ++ch) {
+          const int kc0 = ch * nkb / nchain, kc1 = (ch + 1) * nkb / nchain;
+          // A new item needs both accumulators back from the drain; a later
+          // chain needs only L0, so its first K block issues the L1 MMAs first
+          // and waits for L0 only before its level-0 MMA.
+          if (ch == 0) {
+            if (!mbar_wait(&accempty_bar, aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS);
-            for (int kc = kc0; kc < kc1; ++kc) {
-              if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t sA = smem_u32(sm + stage * STAGE_BYTES);
-              const uint64_t bd = sdesc(sA + S * A_SLICE_BYTES);
-#pragma unroll
-              for (int a = 0; a < S; ++a) {
-                const uint64_t ad = sdesc(sA + a * A_SLICE_BYTES + mh * (A_SLICE_BYTES / 2));
-                const uint32_t dcol = dbase + (uint32_t)(mh * S * 32 + a * np * NT);
-                mma_bf16(dcol, ad, bd, idesc(128, (S - a) * np * NT), (kc > kc0 || a > 0) ? 1u : 0u);
-              }
-              mma_commit(&empty_bar[stage]);
-              if (++stage == B.stages) { stage = 0; phase ^= 1u; }
-            }
-            if (!ok) break;
-            mma_commit(&accfull_bar[abuf]);
-            if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-            }
           }
+          for (int kc = kc0; kc < kc1; ++kc) {
+            if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sA = smem_u32(sm + (size_t)stage * B.slot);
+            const uint32_t sB = sA + S * A_BLK;
+            int n = 0;
+#pragma unroll
+            for (int a = 0; a < S; ++a)
+#pragma unroll
+              for (int b = 0; b < S - a; ++b) {
+                if (a + b == 0) continue;                                          // levels >= 1 -> L1
+                mma_bf16(tbase + (uint32_t)nc, sdesc(sA + a * A_BLK), sdesc(sB + b * bslice), id,
+                         (kc == 0 && n == 0) ? 0u : 1u);
+                ++n;
+              }
+            if (kc == kc0 && ch > 0) {
+              if (!mbar_wait(&accempty_bar, aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            mma_bf16(tbase, sdesc(sA), sdesc(sB), id, kc > kc0 ? 1u : 0u);          // level 0 -> L0
+            mma_commit(&empty_bar[stage]);
+            if (++stage == B.stages) { stage = 0; phase ^= 1u; }
+          }
+          if (!ok) break;
+          mma_commit(&accfull_bar);
+          aphase ^= 1u;
         }
       }
       // all MMAs issued by this thread complete before TMEM is released
-      mma_commit(&teardown_bar[mh]);
-      const uint32_t a = smem_u32(&teardown_bar[mh]);
+      mma_commit(&teardown_bar);
+      const uint32_t a = smem_u32(&teardown_bar);
       for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, 0); ++it) {
         if ((it & 255) == 255) __nanosleep(128);
         if (it == WAIT_LIMIT - 1) atomicCAS(B.err, 0, ERR_TIMEOUT_TEARDOWN);
@@ -448,143 +390,81 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ drain + energy epilogue
-    const int et = tid - 64;                  // 0 .. 255
-    const int quarter = warp & 3;             // TMEM lane quarter this warp may access
-    const int lrow = 32 * quarter + lane;     // row within a 128-row half
-    const int h = et >> 7;                    // warpgroup -> 128-row half of every job
-    int abuf = 0;
+    // ------------------------------------------------------------ drain: TMEM -> tile sum -> Y
+    const int et = tid - 64;                        // 0 .. 255
+    const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;               // which half of the 16-column groups
+    const int lrow = 32 * quarter + lane;           // row of the M tile
+    const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16);
     uint32_t aphase = 0;
     bool ok = true;
     int jc = 0;
-    for (long long gitem = blockIdx.x; ok && gitem < B.total_items; gitem += gridDim.x) {
-      while (jc + 1 < B.njobs && gitem >= B.job[jc + 1].item0) ++jc;   // items ascend: the cursor only moves on
-      const SplitJob &P = B.job[jc];
-      const Dims &d = P.d;
-      const int o = d.o, v = d.v;
-      const long long item = gitem - P.item0 + P.item_base;
-      (void)v;
-      int t, chunk;
-      const long long islot = item_slot(d, item, t, chunk);
-      const int4 tr = P.w.trip[t];
-      const int occ[3] = {tr.x, tr.y, tr.z};
-      const double eijk = __ldg(P.eps + occ[0]) + __ldg(P.eps + occ[1]) + __ldg(P.eps + occ[2]);
-      double acc = 0.0;
-      const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
-      for (int ob = chunk * d.orb_per_item; ok && ob < ob1; ++ob) {
-        const int4 og = P.w.orb[ob];
-        const int tl[3] = {og.x, og.y, og.z};
-        const int pid = pattern_id(occ, tl);
-        const int nj = c_ntjobs[pid];
-        for (int jb = 0; jb < nj; ++jb) {
-          const TJob J = c_tjobs[pid][jb];
-          const int nchain = ((J.kind == 0 ? P.kch_p : P.kch_h) + KCHAIN - 1) / KCHAIN;
-          for (int ch = 0; ch < nchain; ++ch) {
-          if (et == 0)
-            epi_ok = mbar_wait(&accfull_bar[abuf], aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
-          epi_bar();
-          if (!epi_ok) { ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dbase = tbase + (uint32_t)(abuf * BUFCOLS) + ((uint32_t)(32 * quarter) << 16);
-          const int np = J.np;
-          // The two panels of a job may update the same W elements (coincident tiles put
-          // both products in one block with different orientations), so panel 1 starts
-          // only after every thread has finished panel 0.
+    for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
+      while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
+      const WtJob &J = B.job[jc];
+      const int nc = J.g.nc, ys = J.g.ys;
+      const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
+      const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
+      const int ng = nc / 16, gsplit = (ng + 1) / 2;
+      const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
+      float *srow = sum + (size_t)lrow * ys + g0 * 16;
+      // the previous tile's bulk store has finished reading the sum tile
+      if (et == 0) bulk_wait_read();
+      drain_bar();
+      for (int ch = 0; ch < nchain; ++ch) {
+        if (et == 0) drain_ok = mbar_wait(&accfull_bar, aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
+        drain_bar();
+        if (!drain_ok) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // Read the chain's L0 (and on the last chain add L1) into registers,
+        // hand the accumulators back to the MMA warp, then add into the sum.
+        float v[MAXG][16];
 #pragma unroll
-          for (int pn = 0; pn < 2; ++pn) {
-            if (pn >= np) break;
-            if (pn == 1) epi_bar();
-            {
-              const int row = h * 128 + lrow;
-              const int rhi = row >> 4, rlo = row & 15;
-              float lv[S][16];
+        for (int gi2 = 0; gi2 < MAXG; ++gi2)
+          if (gi2 < my) tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), v[gi2]);
+        tmem_wait_ld();
+        if (ch + 1 == nchain) {
 #pragma unroll
-              for (int L = 0; L < S; ++L) tmem_ld16(dbase + (uint32_t)(h * S * 32 + L * np * NT + pn * NT), lv[L]);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-              int lc[3];
-              lc[J.hi[pn]] = rhi;
-              lc[J.lo[pn]] = rlo;
-              lc[J.col[pn]] = 0;
-              const int cstride = (J.col[pn] == 0) ? WX : (J.col[pn] == 1 ? WY : 1);
-              float *base = Wsm + J.blk[pn] * WBLK + lc[0] * WX + lc[1] * WY + lc[2];
+          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+            if (gi2 >= my) break;
+            float l1[16];
+            tmem_ld16(trow + (uint32_t)(nc + (g0 + gi2) * 16), l1);
+            tmem_wait_ld();
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                float sum = lv[S - 1][j];             // smallest level first
-#pragma unroll
-                for (int L = S - 2; L >= 0; --L) sum += lv[L][j];
-                base[j * cstride] += sum;
-              }
-            }
-          }
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          epi_bar();                             // all loads and W updates of this job are done
-          if (et == 0) mbar_arrive(&accempty_bar[abuf]);
-          if (++abuf == 2) { abuf = 0; aphase ^= 1u; }
-          }
-          if (!ok) break;
-        }
-        if (!ok) break;
-
-        // energy over the canonical points a >= b >= c of the orbit
-        int blk[6];
-        orbit_blocks(tl, blk);
-        for (int pr = et; pr < NT * NT; pr += EPI_THREADS) {
-          const int la = pr >> 4, lb = pr & 15;
-          const int ga = tl[0] * NT + la, gb = tl[1] * NT + lb;
-          if (ga >= v || gb >= v || ga < gb) continue;
-          const double dab = eijk - (__ldg(P.eps + o + ga) + __ldg(P.eps + o + gb));
-          for (int lcc = 0; lcc < NT; ++lcc) {
-            const int gc = tl[2] * NT + lcc;
-            if (gc >= v || gb < gc) continue;
-            const int l3[3] = {la, lb, lcc};
-            const int g[3] = {ga, gb, gc};
-            float ws[6], vs[6];
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-              const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
-              ws[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
-              const int x = g[p0], y = g[p1], z = g[p2];
-              const float *ov = P.ovovf;
-              vs[s] = __ldg(P.t1f + occ[0] * v + x) * __ldg(ov + ((occ[1] * v + y) * o + occ[2]) * v + z)
-                    + __ldg(P.t1f + occ[1] * v + y) * __ldg(ov + ((occ[0] * v + x) * o + occ[2]) * v + z)
-                    + __ldg(P.t1f + occ[2] * v + z) * __ldg(ov + ((occ[0] * v + x) * o + occ[1]) * v + y);
-            }
-            const float se = ws[0] + ws[3] + ws[4];
-            const float so = ws[1] + ws[2] + ws[5];
-            float sum = 0.f;
-#pragma unroll
-            for (int s = 0; s < 6; ++s) {
-              const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
-              sum = fmaf(ws[s] + vs[s], br, sum);
-            }
-            // FP64 denominator: D = e_i + e_j + e_k - e_a - e_b - e_c and 1/D by one
-            // Newton-Raphson step from the hardware reciprocal estimate.
-            const double D = dab - __ldg(P.eps + o + gc);
-            double r;
-            asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(D));
-            r = fma(r, fma(-D, r, 1.0), r);
-            const double mult = (ga == gc) ? (1.0 / 6.0) : ((ga == gb || gb == gc) ? 0.5 : 1.0);
-            acc = fma((double)sum * mult, r, acc);
+            for (int e = 0; e < 16; ++e) v[gi2][e] += l1[e];
           }
         }
-        epi_bar();
-        for (int e = et; e < 6 * WBLK; e += EPI_THREADS) Wsm[e] = 0.f;
-        epi_bar();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        drain_bar();
+        if (et == 0) mbar_arrive(&accempty_bar);
+#pragma unroll
+        for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+          if (gi2 >= my) break;
+          float4 *d4 = (float4 *)(srow + gi2 * 16);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float4 x = make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
+            if (ch > 0) {
+              const float4 s0 = d4[e];
+              x.x += s0.x; x.y += s0.y; x.z += s0.z; x.w += s0.w;
+            }
+            d4[e] = x;
+          }
+        }
+        aphase ^= 1u;
       }
       if (!ok) break;
-      // the item's partial: fixed-order reduction over the 128 epilogue threads
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) red[warp - 2] = acc;
-      epi_bar();
+      // the finished tile leaves with one bulk store
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      drain_bar();
       if (et == 0) {
-        double tot = 0.0;
-#pragma unroll
-        for (int wq = 0; wq < EPI_WARPS; ++wq) tot += red[wq];
-        P.w.partial[islot] = tot;
+        int m, tl, g, nci;
+        wt_decode(J, gi - J.item0, m, tl, g, nci);
+        const size_t tile = (((size_t)tl * 3 + g) * J.g.nch + nci) * J.g.mt + m;
+        bulk_store(J.y + tile * MROWS * ys, sum, (uint32_t)(MROWS * ys * 4));
       }
-      epi_bar();
     }
+    if (et == 0) bulk_wait_all();
   }
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -595,65 +475,227 @@ tc_split_kernel(const __grid_constant__ SplitBatch B) {
   }
 }
 
+// ---------------------------------------------------------------- energy kernel
+
+__global__ void __launch_bounds__(EN_THREADS, 2)
+tc_energy_kernel(const __grid_constant__ EnBatch B) {
+  extern __shared__ __align__(16) float Wsm[];     // 6 W blocks
+  __shared__ double red[EN_THREADS / 32];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int jc = 0;
+  for (long long gi = blockIdx.x; gi < B.total_items; gi += gridDim.x) {
+    while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
+    const EnJob &J = B.job[jc];
+    const Dims &d = J.d;
+    const SplitGeom &G = J.g;
+    const int o = d.o, v = d.v;
+    const long long q = gi - J.item0;
+    const int tl = (int)(q / d.items_per_trip), chunk = (int)(q % d.items_per_trip);
+    const int t = J.t0 + tl;
+    const int4 tr = J.trip[t];
+    const int occ[3] = {tr.x, tr.y, tr.z};
+    const double eijk = __ldg(J.eps + occ[0]) + __ldg(J.eps + occ[1]) + __ldg(J.eps + occ[2]);
+    // F buffer g of this triplet: rows (x, y) = x v + y, column z
+    const size_t fstride = (size_t)G.nch * G.mt * MROWS * G.ys;
+    const float *Yt = J.y + (size_t)tl * 3 * fstride;
+    double acc = 0.0;
+    const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
+    for (int ob = chunk * d.orb_per_item; ob < ob1; ++ob) {
+      const int4 og = J.orb[ob];
+      const int tl3[3] = {og.x, og.y, og.z};
+      int blk[6];
+      orbit_blocks(tl3, blk);
+      // W_abc = F(i,j,k)[ab,c] + F(i,k,j)[ac,b] + F(j,k,i)[bc,a]: one pass per F,
+      // 16-byte loads along the F's contiguous index (its column), the loads of
+      // three blocks in flight before their shared-memory writes.  Rows with an
+      // index >= v are 0; columns >= v read the W-term GEMM's zero padding.
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass) {
+        const float *Yg = Yt + pass * fstride;
+#pragma unroll 1
+        for (int s0 = 0; s0 < 6; s0 += 3) {
+          float4 val[3][4];
+#pragma unroll
+          for (int si = 0; si < 3; ++si) {
+            const int s = s0 + si;
+            const int X = tl3[perm3(s, 0)] * NT, Y = tl3[perm3(s, 1)] * NT, Z = tl3[perm3(s, 2)] * NT;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int f = tid + EN_THREADS * u;            // float4 index in the block, 0 .. 1023
+              const int hi = f >> 6, mid = (f >> 2) & 15, lo = (f & 3) * 4;
+              int r0, r1, col;                               // row = r0 * v + r1
+              if (pass == 0)      { r0 = X + hi; r1 = Y + mid; col = Z + lo; }
+              else if (pass == 1) { r0 = X + hi; r1 = Z + mid; col = Y + lo; }
+              else                { r0 = Y + hi; r1 = Z + mid; col = X + lo; }
+              float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (blk[s] == s && r0 < v && r1 < v) {
+                const int nci = col / G.nc;
+                x = __ldg((const float4 *)(Yg + ((size_t)nci * G.mt * MROWS + (size_t)r0 * v + r1) * G.ys +
+                                           (col - nci * G.nc)));
+              }
+              val[si][u] = x;
+            }
+          }
+#pragma unroll
+          for (int si = 0; si < 3; ++si) {
+            const int s = s0 + si;
+            if (blk[s] != s) continue;
+            float *Wb = Wsm + s * WBLK;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int f = tid + EN_THREADS * u;
+              const int hi = f >> 6, mid = (f >> 2) & 15, lo = (f & 3) * 4;
+              // the four points of the load differ in the F's column index
+              float *w;
+              int step;
+              if (pass == 0)      { w = Wb + hi * WX + mid * WY + lo; step = 1; }
+              else if (pass == 1) { w = Wb + hi * WX + lo * WY + mid; step = WY; }
+              else                { w = Wb + lo * WX + hi * WY + mid; step = WX; }
+              const float4 x = val[si][u];
+              if (pass == 0) {
+                w[0] = x.x; w[step] = x.y; w[2 * step] = x.z; w[3 * step] = x.w;
+              } else {
+                w[0] += x.x; w[step] += x.y; w[2 * step] += x.z; w[3 * step] += x.w;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+
+      // energy over the canonical points a >= b >= c of the orbit
+      for (int pr = tid; pr < NT * NT; pr += EN_THREADS) {
+        const int la = pr >> 4, lb = pr & 15;
+        const int ga = tl3[0] * NT + la, gb = tl3[1] * NT + lb;
+        if (ga >= v || gb >= v || ga < gb) continue;
+        const double dab = eijk - (__ldg(J.eps + o + ga) + __ldg(J.eps + o + gb));
+        float rowsum = 0.f;                // the row's up to 16 points, added into acc in FP64 once
+        for (int lcc = 0; lcc < NT; ++lcc) {
+          const int gc = tl3[2] * NT + lcc;
+          if (gc >= v || gb < gc) continue;
+          const int l3[3] = {la, lb, lcc};
+          const int g3[3] = {ga, gb, gc};
+          float ws[6], vs[6];
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
+            ws[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
+            const int x = g3[p0], y = g3[p1], z = g3[p2];
+            const float *ov = J.ovovf;
+            vs[s] = __ldg(J.t1f + occ[0] * v + x) * __ldg(ov + ((occ[1] * v + y) * o + occ[2]) * v + z)
+                  + __ldg(J.t1f + occ[1] * v + y) * __ldg(ov + ((occ[0] * v + x) * o + occ[2]) * v + z)
+                  + __ldg(J.t1f + occ[2] * v + z) * __ldg(ov + ((occ[0] * v + x) * o + occ[1]) * v + y);
+          }
+          const float se = ws[0] + ws[3] + ws[4];
+          const float so = ws[1] + ws[2] + ws[5];
+          float sumf = 0.f;
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
+            sumf = fmaf(ws[s] + vs[s], br, sumf);
+          }
+          // D = e_i + e_j + e_k - e_a - e_b - e_c formed in FP64 (no cancellation
+          // loss), its correctly rounded FP32 reciprocal
+          const double D = dab - __ldg(J.eps + o + gc);
+          const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
+          rowsum = fmaf(sumf * mult, __frcp_rn((float)D), rowsum);
+        }
+        acc += (double)rowsum;
+      }
+      __syncthreads();                    // W is rebuilt by the next orbit
+    }
+    // the item's partial: fixed-order reduction over the block
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int wq = 0; wq < EN_THREADS / 32; ++wq) tot += red[wq];
+      J.partial[(long long)t * d.items_per_trip + chunk] = tot;
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- operand images
 
-// One thread per (image, row, K half): reads 8 consecutive K values of one
+// One thread per (block, K half, row): reads 8 consecutive K values of one
 // operand row, splits them into S BF16 slices and writes 16 bytes per slice at
-// the row's place in the no-swizzle K-major image.  Rows or K values outside
-// the tensor are zero.
-//   mode 0: A particle  image (x, ta, tb, kb), row (a, b), K = f:  (x a | b f)
-//   mode 1: A hole      image (z, ta, tb, kb), row (a, b), K = l:  t2[l][z][a][b]
-//   mode 2: B particle  image (y, z, tc, kb),  row c,      K = f:  t2[y][z][c][f]
-//   mode 3: B hole      image (x, y, tc, kb),  row c,      K = l:  -(x c | y l)
-__global__ void build_images(int mode, const double *__restrict__ src, int o, int v, int T, int nkb, int S,
-                             unsigned char *__restrict__ out) {
-  const int rows = (mode < 2) ? 256 : 16;
-  const int img_bytes = rows * KC * 2;
-  const long long nimg = (long long)((mode == 0 || mode == 1) ? o * T * T : o * o * T) * nkb;
-  const long long total = nimg * rows * 2;
+// the row's place in the no-swizzle K-major block.  Rows or K values outside
+// the tensors are zero.
+//   kind 0  A  [p][m][kb]        row (x, y), K f:  (p x | y f)            = ovvv[p][x][y][f]
+//   kind 1  A  [p][m][kb]        row (x, y), K f:  (p y | x f)            = ovvv[p][y][x][f]
+//   kind 2  A  [p][m][kb]        row (x, y), K l:  t_lp^xy = t_pl^yx      = t2[p][l][y][x]
+//   kind 3  A  [p][m][kb]        row (x, y), K l:  t_lp^yx = t_pl^xy      = t2[p][l][x][y]
+//   kind 4  B  [r][q][nc][kb]    row z,      K f:  t_rq^zf                = t2[r][q][z][f]
+//   kind 5  B  [r][q][nc][kb]    row z,      K l:  -(r z | q l)           = -ovoo[r][z][q][l]
+// (kinds 2 and 3 read t_lp^.. as t_pl^.. with the virtual pair swapped, which
+// keeps the reads coalesced).
+__global__ void build_image(int kind, const double *__restrict__ src, SplitGeom G, unsigned char *__restrict__ out) {
+  const int o = G.o, v = G.v, S = G.S;
+  const bool isA = kind < 4;
+  const int rows = isA ? MROWS : G.nc;
+  const int kbx = (kind == 0 || kind == 1 || kind == 4) ? G.kbv : G.kbo;
+  const int kmax = (kind == 0 || kind == 1 || kind == 4) ? v : o;
+  const long long nblk = isA ? (long long)o * G.mt * kbx : (long long)o * o * G.nch * kbx;
+  const size_t blk_bytes = (size_t)rows * KB * 2;
+  const long long total = nblk * 2 * rows;
   const long long vv = (long long)v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int kh = (int)(e & 1);
-    const int r = (int)((e >> 1) % rows);
-    const long long img = (e >> 1) / rows;
-    const int kb = (int)(img % nkb);
-    const long long rest = img / nkb;                      // (.., .., tile) or (.., tile, tile)
+    const int r = (int)(e % rows);
+    const int kh = (int)((e / rows) & 1);
+    const long long blk = e / (2 * rows);
+    const int kb = (int)(blk % kbx);
+    const long long rest = blk / kbx;
+    const int k0 = kb * KB + kh * 8;
     double x[8];
-    int k0 = kb * KC + kh * 8;
-    if (mode < 2) {
-      const int tb = (int)(rest % T), ta = (int)((rest / T) % T), xo = (int)(rest / ((long long)T * T));
-      const int a = ta * NT + r / NT, b = tb * NT + r % NT;
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + q;
+    if (isA) {
+      const int m = (int)(rest % G.mt);
+      const long long p = rest / G.mt;
+      const long long row = (long long)m * MROWS + r;
+      const bool valid = row < vv;
+      const long long xi = valid ? row / v : 0, yi = valid ? row % v : 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
         double val = 0.0;
-        if (mode == 0) { if (a < v && b < v && k < v) val = src[((long long)xo * v + a) * vv + (long long)b * v + k]; }
-        else           { if (a < v && b < v && k < o) val = src[((long long)k * o + xo) * vv + (long long)a * v + b]; }
-        x[q] = val;
+        if (valid && k < kmax) {
+          if (kind == 0)      val = src[((p * v + xi) * v + yi) * v + k];
+          else if (kind == 1) val = src[((p * v + yi) * v + xi) * v + k];
+          else if (kind == 2) val = src[((p * o + k) * v + yi) * v + xi];
+          else                val = src[((p * o + k) * v + xi) * v + yi];
+        }
+        x[u] = val;
       }
     } else {
-      const int tc = (int)(rest % T);
-      const long long pair = rest / T;                     // y*o + z  or  x*o + y
-      const int p0 = (int)(pair / o), p1 = (int)(pair % o);
-      const int c = tc * NT + r;
-      for (int q = 0; q < 8; ++q) {
-        const int k = k0 + q;
+      const int nci = (int)(rest % G.nch);
+      const long long pair = rest / G.nch;               // r * o + q
+      const long long rr = pair / o, qq = pair % o;
+      const int z = nci * G.nc + r;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
         double val = 0.0;
-        if (mode == 2) { if (c < v && k < v) val = src[(((long long)p0 * o + p1) * v + c) * v + k]; }
-        else           { if (c < v && k < o) val = -src[(((long long)p0 * v + c) * o + p1) * o + k]; }
-        x[q] = val;
+        if (z < v && k < kmax) {
+          if (kind == 4) val = src[((rr * o + qq) * v + z) * v + k];
+          else           val = -src[((rr * v + z) * o + qq) * o + k];
+        }
+        x[u] = val;
       }
     }
-    // position of (row r, K half kh) in the image: core matrix (r/8, kh), row r%8
+    // position of (row r, K half kh) in the block: core matrix (r/8, kh), row r%8
     const int off = ((r >> 3) * 2 + kh) * 128 + (r & 7) * 16;
-    unsigned char *base = out + (size_t)img * S * img_bytes + off;
+    unsigned char *base = out + (size_t)blk * S * blk_bytes + off;
     for (int p = 0; p < S; ++p) {
       __align__(16) __nv_bfloat16 b16[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        b16[q] = __double2bfloat16(x[q]);
-        x[q] -= (double)__bfloat162float(b16[q]);        // exact FP64 residual
+      for (int u = 0; u < 8; ++u) {
+        b16[u] = __double2bfloat16(x[u]);
+        x[u] -= (double)__bfloat162float(b16[u]);        // exact FP64 residual
       }
-      *(uint4 *)(base + (size_t)p * img_bytes) = *(const uint4 *)b16;
+      *(uint4 *)(base + (size_t)p * blk_bytes) = *(const uint4 *)b16;
     }
   }
 }
@@ -663,54 +705,76 @@ __global__ void to_f32(const double *__restrict__ in, long long n, float *__rest
     out[e] = (float)in[e];
 }
 
-int stages_for(int S) {
-  const int stage_bytes = S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES);
-  const int budget = 227 * 1024 - W_BYTES - 1024 - 256;
-  int st = budget / stage_bytes;
-  if (st > MAX_STAGES) st = MAX_STAGES;
-  // The producers' parity waits on the empty barriers stay unambiguous only
-  // while a producer can be at most one ring cycle ahead of the stage's last
-  // use, which the in-order MMA consumer guarantees when stages >= NPROD.
-  static_assert((227 * 1024 - W_BYTES - 1024 - 256) / (MAXS * (A_SLICE_BYTES + 2 * B_PANEL_BYTES)) >= NPROD,
-                "fewer pipeline stages than producer warps");
-  return st;
-}
+// ---------------------------------------------------------------- host side
 
-size_t smem_for(int S) {
-  return (size_t)stages_for(S) * S * (A_SLICE_BYTES + 2 * B_PANEL_BYTES) + W_BYTES + 1024;
+struct WtShape {
+  int stages, nprod;
+  size_t slot, sum_off, smem;
+};
+
+// Shared-memory plan of a W-term launch whose widest N chunk is ncmax.
+WtShape wt_shape(int S, int ncmax) {
+  WtShape s{};
+  s.slot = (size_t)S * A_BLK + (size_t)S * ncmax * 32;
+  const size_t sum_bytes = (size_t)MROWS * (ncmax + 4) * 4;
+  const long long st = ((long long)SMEM_DYN_MAX - 1024 - (long long)sum_bytes) / (long long)s.slot;
+  s.stages = (int)std::min<long long>(MAX_STAGES, st);
+  // The producers' parity waits on the empty barriers stay unambiguous only
+  // while a producer is at most one ring cycle ahead of a stage's last use,
+  // which the in-order MMA consumer guarantees when stages >= producers.
+  s.nprod = std::min(NPROD, s.stages);
+  s.sum_off = (size_t)s.stages * s.slot;
+  s.smem = 1024 + s.sum_off + sum_bytes;
+  return s;
 }
 
 template <int S>
-cudaError_t launch_kernel(long long grid, size_t smem, cudaStream_t st, const SplitBatch &b) {
-  cudaError_t e = cudaFuncSetAttribute(tc_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  tc_split_kernel<S><<<(int)grid, THREADS, smem, st>>>(b);
-  return cudaGetLastError();
+void wt_params(const WtBatch &b, int grid, size_t smem, void **args, cudaKernelNodeParams *p) {
+  args[0] = (void *)&b;
+  *p = cudaKernelNodeParams{};
+  p->func = (void *)tc_wterm_kernel<S>;
+  p->gridDim = dim3(grid);
+  p->blockDim = dim3(THREADS);
+  p->sharedMemBytes = (unsigned)smem;
+  p->kernelParams = args;
 }
 
-// The 12 job templates, built on the host once and copied to constant memory
-// once per device.
-cudaError_t upload_templates(cudaStream_t st) {
-  static std::mutex mu;
-  static bool done[64] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
-  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-  static TJob h[N_PATTERNS][MAX_JOBS];
-  static int hn[N_PATTERNS];
-  const int occ_rep[3][3] = {{2, 1, 0}, {1, 1, 0}, {1, 0, 0}};
-  const int tl_rep[4][3] = {{2, 1, 0}, {1, 1, 0}, {1, 0, 0}, {0, 0, 0}};
-  for (int op = 0; op < 3; ++op)
-    for (int tp = 0; tp < 4; ++tp) {
-      const int pid = pattern_id(occ_rep[op], tl_rep[tp]);
-      hn[pid] = host_build_template(occ_rep[op], tl_rep[tp], h[pid]);
-    }
-  e = cudaMemcpyToSymbolAsync(c_tjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ntjobs, hn, sizeof(hn), 0, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+// Item offsets, shared-memory plan and grids of a W-term batch and an energy
+// batch; sets the kernels' shared-memory limits.
+cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, int *egrid, size_t *wsmem) {
+  if (S < 2 || S > MAXS || wb.njobs < 1 || wb.njobs > MAX_BATCH || eb.njobs != wb.njobs) return cudaErrorInvalidValue;
+  long long total = 0;
+  int ncmax = 16;
+  for (int j = 0; j < wb.njobs; ++j) {
+    WtJob &J = wb.job[j];
+    if (J.g.nc > NCMAX || J.g.S != S) return cudaErrorInvalidValue;
+    J.item0 = total;
+    total += (long long)J.g.mt * J.nt * 3 * J.g.nch;
+    ncmax = std::max(ncmax, J.g.nc);
+  }
+  wb.total_items = total;
+  const WtShape sh = wt_shape(S, ncmax);
+  if (sh.stages < 2) return cudaErrorInvalidValue;
+  wb.stages = sh.stages;
+  wb.nprod = sh.nprod;
+  wb.slot = sh.slot;
+  wb.sum_off = sh.sum_off;
+  *wsmem = sh.smem;
+  long long etotal = 0;
+  for (int j = 0; j < eb.njobs; ++j) {
+    eb.job[j].item0 = etotal;
+    etotal += (long long)eb.job[j].nt * eb.job[j].d.items_per_trip;
+  }
+  eb.total_items = etotal;
+  *wgrid = (int)std::max<long long>(1, std::min<long long>(num_sms, total));
+  *egrid = (int)std::max<long long>(1, std::min<long long>(2LL * num_sms, etotal));
+  cudaError_t e = cudaSuccess;
+  switch (S) {
+    case 2: e = cudaFuncSetAttribute(tc_wterm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
+    case 3: e = cudaFuncSetAttribute(tc_wterm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
+    default: e = cudaFuncSetAttribute(tc_wterm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
+  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EN_SMEM);
   return e;
 }
 
@@ -718,113 +782,137 @@ cudaError_t upload_templates(cudaStream_t st) {
 
 int split_tile() { return NT; }
 
+SplitGeom split_geom(int o, int v, int S) {
+  SplitGeom g{};
+  g.o = o;
+  g.v = v;
+  g.S = S;
+  g.mt = (int)(((long long)v * v + MROWS - 1) / MROWS);
+  g.kbv = (v + KB - 1) / KB;
+  g.kbo = (o + KB - 1) / KB;
+  const int vp = g.kbv * KB;
+  g.nch = (vp + NCMAX - 1) / NCMAX;
+  g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
+  g.ys = g.nc + 4;
+  // Triplets per block: about 16 W-term items per SM of a 152-SM GPU, at most
+  // 64 and at most the number of triplets.
+  const long long per_trip = 3LL * g.mt * g.nch;
+  long long nb = (16LL * 152 + per_trip - 1) / per_trip;
+  nb = std::max<long long>(1, std::min<long long>(64, nb));
+  const long long ntrip = std::max<long long>(1, (long long)o * (o + 1) * (o + 2) / 6 - o);
+  g.nb = (int)std::min(nb, ntrip);
+  return g;
+}
+
 SplitLayout split_layout(int o, int v, int S) {
   SplitLayout L{};
-  const long long T = (v + NT - 1) / NT, nkb = (v + KC - 1) / KC, nko = (o + KC - 1) / KC;
-  L.vpad = (int)(T * NT);
-  L.opad = (int)(nko * KC);
+  const SplitGeom g = split_geom(o, v, S);
+  L.g = g;
+  const size_t a_v = (size_t)o * g.mt * g.kbv * S * A_BLK, a_o = (size_t)o * g.mt * g.kbo * S * A_BLK;
+  const size_t b_v = (size_t)o * o * g.nch * g.kbv * S * g.nc * 32, b_o = (size_t)o * o * g.nch * g.kbo * S * g.nc * 32;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~(size_t)255; return r; };
-  L.ovvv = take((size_t)o * T * T * nkb * S * A_SLICE_BYTES);     // A particle images
-  L.t2h = take((size_t)o * T * T * nko * S * A_SLICE_BYTES);      // A hole images
-  L.t2 = take((size_t)o * o * T * nkb * S * B_PANEL_BYTES);       // B particle images
-  L.ovoo = take((size_t)o * o * T * nko * S * B_PANEL_BYTES);     // B hole images
+  L.pa = take(a_v);
+  L.pa2 = take(a_v);
+  L.hc = take(a_o);
+  L.hc2 = take(a_o);
+  L.tb = take(b_v);
+  L.hb = take(b_o);
   L.t1f = take((size_t)o * v * 4);
   L.ovovf = take((size_t)o * v * o * v * 4);
+  L.y = take((size_t)g.nb * 3 * g.nch * g.mt * MROWS * g.ys * 4);
   L.total = off;
   return L;
 }
 
-cudaError_t launch_split_prep(const Dims &d, int S, const Inputs &in, void *ws, const SplitLayout &L, cudaStream_t st) {
-  const int o = d.o, v = d.v;
-  const int T = (v + NT - 1) / NT, nkb = (v + KC - 1) / KC, nko = (o + KC - 1) / KC;
+cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st) {
+  const SplitGeom &g = L.g;
   unsigned char *b = (unsigned char *)ws;
   const int blocks = 152 * 16, thr = 256;
-  build_images<<<blocks, thr, 0, st>>>(0, in.ovvv, o, v, T, nkb, S, b + L.ovvv);
-  build_images<<<blocks, thr, 0, st>>>(1, in.t2, o, v, T, nko, S, b + L.t2h);
-  build_images<<<blocks, thr, 0, st>>>(2, in.t2, o, v, T, nkb, S, b + L.t2);
-  build_images<<<blocks, thr, 0, st>>>(3, in.ovoo, o, v, T, nko, S, b + L.ovoo);
-  to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)o * v, (float *)(b + L.t1f));
-  to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)o * v * o * v, (float *)(b + L.ovovf));
+  build_image<<<blocks, thr, 0, st>>>(0, in.ovvv, g, b + L.pa);
+  build_image<<<blocks, thr, 0, st>>>(1, in.ovvv, g, b + L.pa2);
+  build_image<<<blocks, thr, 0, st>>>(2, in.t2, g, b + L.hc);
+  build_image<<<blocks, thr, 0, st>>>(3, in.t2, g, b + L.hc2);
+  build_image<<<blocks, thr, 0, st>>>(4, in.t2, g, b + L.tb);
+  build_image<<<blocks, thr, 0, st>>>(5, in.ovoo, g, b + L.hb);
+  to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)g.o * g.v, (float *)(b + L.t1f));
+  to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)g.o * g.v * g.o * g.v, (float *)(b + L.ovovf));
   return cudaGetLastError();
 }
 
-SplitJob split_job(const Dims &d, const Inputs &in, const void *ws, const SplitLayout &L, const Work &w) {
-  const int o = d.o, v = d.v;
+int split_prep_launches() { return 8; }
+
+WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt) {
   const unsigned char *b = (const unsigned char *)ws;
-  SplitJob P{};
-  P.d = d;
-  P.kch_p = (v + KC - 1) / KC;
-  P.kch_h = (o + KC - 1) / KC;
-  P.T = (v + NT - 1) / NT;
-  P.imgA_p = b + L.ovvv;
-  P.imgA_h = b + L.t2h;
-  P.imgB_p = b + L.t2;
-  P.imgB_h = b + L.ovoo;
-  P.t1f = (const float *)(b + L.t1f);
-  P.ovovf = (const float *)(b + L.ovovf);
-  P.eps = in.eps;
-  P.w = w;
-  return P;
+  WtJob J{};
+  J.g = L.g;
+  J.trip = trip;
+  J.t0 = t0;
+  J.nt = nt;
+  J.pa = b + L.pa;
+  J.pa2 = b + L.pa2;
+  J.hc = b + L.hc;
+  J.hc2 = b + L.hc2;
+  J.tb = b + L.tb;
+  J.hb = b + L.hb;
+  J.y = (float *)(b + L.y);
+  return J;
 }
 
-// Launch one persistent kernel over the batch's items (item0 and total_items
-// are filled in here from the jobs' item counts).
-template <int S>
-void node_params(const SplitBatch &b, int grid, void **args, cudaKernelNodeParams *p) {
-  args[0] = (void *)&b;
-  *p = cudaKernelNodeParams{};
-  p->func = (void *)tc_split_kernel<S>;
-  p->gridDim = dim3(grid);
-  p->blockDim = dim3(THREADS);
-  p->sharedMemBytes = (unsigned)smem_for(S);
-  p->kernelParams = args;
+EnJob en_job(const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w, int t0, int nt) {
+  const unsigned char *b = (const unsigned char *)ws;
+  EnJob J{};
+  J.d = d;
+  J.g = L.g;
+  J.trip = w.trip;
+  J.orb = w.orb;
+  J.eps = in.eps;
+  J.t1f = (const float *)(b + L.t1f);
+  J.ovovf = (const float *)(b + L.ovovf);
+  J.y = (const float *)(b + L.y);
+  J.partial = w.partial;
+  J.t0 = t0;
+  J.nt = nt;
+  return J;
 }
 
-cudaError_t split_node_params(SplitBatch &b, int S, int grid, void **args, cudaKernelNodeParams *p, cudaStream_t st) {
-  if (S < 2 || S > MAXS || b.njobs < 1 || b.njobs > MAX_BATCH) return cudaErrorInvalidValue;
-  long long total = 0;
-  for (int j = 0; j < b.njobs; ++j) {
-    b.job[j].item0 = total;
-    total += b.job[j].n_run > 0 ? b.job[j].n_run : b.job[j].d.n_items;
-  }
-  b.total_items = total;
-  b.stages = stages_for(S);
-  cudaError_t e = upload_templates(st);
+cudaError_t split_block_params(WtBatch &wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
+                               cudaKernelNodeParams *wp, cudaKernelNodeParams *ep) {
+  int wgrid = 1, egrid = 1;
+  size_t wsmem = 0;
+  cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
   if (e != cudaSuccess) return e;
-  const size_t smem = smem_for(S);
   switch (S) {
-    case 2: e = cudaFuncSetAttribute(tc_split_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            node_params<2>(b, grid, args, p); break;
-    case 3: e = cudaFuncSetAttribute(tc_split_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            node_params<3>(b, grid, args, p); break;
-    default: e = cudaFuncSetAttribute(tc_split_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-             node_params<4>(b, grid, args, p); break;
+    case 2: wt_params<2>(wb, wgrid, wsmem, wargs, wp); break;
+    case 3: wt_params<3>(wb, wgrid, wsmem, wargs, wp); break;
+    default: wt_params<4>(wb, wgrid, wsmem, wargs, wp); break;
   }
-  return e;
+  eargs[0] = (void *)&eb;
+  *ep = cudaKernelNodeParams{};
+  ep->func = (void *)tc_energy_kernel;
+  ep->gridDim = dim3(egrid);
+  ep->blockDim = dim3(EN_THREADS);
+  ep->sharedMemBytes = EN_SMEM;
+  ep->kernelParams = eargs;
+  return cudaSuccess;
 }
 
-cudaError_t launch_split(SplitBatch &b, int S, int num_sms, cudaStream_t st) {
-  if (S < 2 || S > MAXS || b.njobs < 1 || b.njobs > MAX_BATCH) return cudaErrorInvalidValue;
-  long long total = 0;
-  for (int j = 0; j < b.njobs; ++j) {
-    b.job[j].item0 = total;
-    total += b.job[j].n_run > 0 ? b.job[j].n_run : b.job[j].d.n_items;
-  }
-  b.total_items = total;
-  b.stages = stages_for(S);
-  const size_t smem = smem_for(S);
-  cudaError_t e = upload_templates(st);
+cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cudaStream_t st,
+                               cudaEvent_t w0, cudaEvent_t w1) {
+  int wgrid = 1, egrid = 1;
+  size_t wsmem = 0;
+  cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
   if (e != cudaSuccess) return e;
-  long long grid = num_sms;
-  if (grid > total) grid = total;
-  if (grid < 1) return cudaSuccess;
+  if (w0 && (e = cudaEventRecord(w0, st)) != cudaSuccess) return e;
   switch (S) {
-    case 2: e = launch_kernel<2>(grid, smem, st, b); break;
-    case 3: e = launch_kernel<3>(grid, smem, st, b); break;
-    default: e = launch_kernel<4>(grid, smem, st, b); break;
+    case 2: tc_wterm_kernel<2><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+    case 3: tc_wterm_kernel<3><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+    default: tc_wterm_kernel<4><<<wgrid, THREADS, wsmem, st>>>(wb); break;
   }
-  return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (w1 && (e = cudaEventRecord(w1, st)) != cudaSuccess) return e;
+  tc_energy_kernel<<<egrid, EN_THREADS, EN_SMEM, st>>>(eb);
+  return cudaGetLastError();
 }
 
 }  // namespace tc

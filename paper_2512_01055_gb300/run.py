@@ -2,9 +2,9 @@
 
     python -m paper_2512_01055_gb300.run --o 8 --v 128 [--prec fp64|split] [--slices 3] [--repeat 1] [--seed 7]
 
-Prints one line per call: E_T, wall seconds, fused-kernel seconds and the
-algorithmic TFLOP/s.  Used for quick runs and as the target of profiler
-captures on small cases.
+Prints one line per call: E_T, wall seconds, kernel seconds (all W/V/energy
+kernels, and the W-forming kernels alone) and the algorithmic TFLOP/s.  Used
+for quick runs and as the target of profiler captures on small cases.
 """
 import argparse
 import os
@@ -40,7 +40,8 @@ def main(argv=None):
             r = tc.tc_energy_dev(ctx, a.o, a.v, dev["eps"], dev["t1"], dev["t2"], dev["ovvv"], dev["ovoo"],
                                  dev["ovov"], prec=prec, slices=a.slices if prec else 0)
             print(f"o={a.o} v={a.v} prec={a.prec} E_T={r.e_t:.15e} wall_s={r.seconds:.4f} "
-                  f"kernel_s={r.kernel_seconds:.4f} prep_s={r.prep_seconds:.4f} TFLOP/s={r.tflops_alg:.3f}")
+                  f"kernel_s={r.kernel_seconds:.4f} wterm_s={r.wterm_seconds:.4f} prep_s={r.prep_seconds:.4f} "
+                  f"TFLOP/s={r.tflops_alg:.3f}")
     finally:
         tc.tc_finalize(ctx)
 
