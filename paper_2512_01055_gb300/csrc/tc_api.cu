@@ -115,7 +115,8 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
         wb.job[0] = tc::wt_job(SL, ctx->ws_split.p, w.trip, t0, nt);
         eb = tc::EnBatch{};
         eb.njobs = 1;
-        eb.job[0] = tc::en_job(d, SL, ctx->ws_split.p, in, w, t0, nt);
+        eb.err = w.err;
+        TC_CUDA(ctx, tc::en_job(&eb.job[0], d, SL, ctx->ws_split.p, in, w, t0, nt));
         TC_CUDA(ctx, tc::launch_split_block(wb, eb, slices, ctx->num_sms, st, ctx->wev[2 * blk], ctx->wev[2 * blk + 1]));
       }
       launches += 2 * nblocks - 1;

@@ -18,6 +18,7 @@
 // any batch.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tc {
@@ -89,7 +90,8 @@ struct SplitGeom {
   int mt;                // M tiles: ceil(v^2 / 128)
   int kbv, kbo;          // K blocks over a virtual / an occupied index
   int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
-  int ys;                // row stride of a W-term tile in floats (nc + 4)
+  int ys;                // row stride of a W-term tile in shared memory, floats (nc + 4)
+  int vc;                // innermost extent of the W-term buffer (v rounded up to 4)
   int nb;                // triplets per block (capacity of the W-term buffer)
 };
 // Byte offsets of the operand images, FP32 copies and W-term buffer inside a
@@ -104,7 +106,7 @@ struct WtJob {           // one job's block of triplets in a W-term launch
   const int4 *trip;      // the job's triplet table
   int t0, nt;            // triplets [t0, t0 + nt) of the table
   const unsigned char *pa, *pa2, *hc, *hc2, *tb, *hb;
-  float *y;              // W-term buffer [nt][3][nch][mt * 128][ys]
+  float *y;              // W-term buffer [nt][3][a][b][vc]: F(i,j,k)[ab,c], F(i,k,j)[ac,b], F(j,k,i)[bc,a] at c
   long long item0;       // first global item of this job in the launch (set by the launcher)
 };
 struct WtBatch {
@@ -116,6 +118,7 @@ struct WtBatch {
   WtJob job[MAX_BATCH];
 };
 struct EnJob {           // one job's block of triplets in an energy launch
+  CUtensorMap ymap;      // 4-D map of the W-term buffer: (c, b, a, 3 * triplet + F)
   Dims d;
   SplitGeom g;
   const int4 *trip, *orb;
@@ -128,6 +131,7 @@ struct EnJob {           // one job's block of triplets in an energy launch
 struct EnBatch {
   int njobs;
   long long total_items;
+  int *err;
   EnJob job[MAX_BATCH];
 };
 int split_tile();
@@ -136,7 +140,9 @@ SplitLayout split_layout(int o, int v, int S);
 cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st);
 int split_prep_launches();
 WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt);
-EnJob en_job(const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w, int t0, int nt);
+// Energy job of triplets [t0, t0 + nt); encodes its tensor map (driver entry point).
+cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w,
+                   int t0, int nt);
 // One block of triplets: the W-term launch, then the energy launch, on st.
 // w0 / w1 (optional) are recorded around the W-term launch.
 cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cudaStream_t st,

@@ -290,17 +290,17 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     wb = WtBatch{};
     eb = EnBatch{};
     wb.njobs = eb.njobs = nj;
-    wb.err = d_err;
+    wb.err = eb.err = d_err;
     for (int j = 0; j < nj; ++j) {
       Req &q = *jobs[j];
       const Inputs in{q.din[0], q.din[1], q.din[2], q.din[3], q.din[4], q.din[5]};
       const int t0 = (int)q.next_item, nt = (int)take[j];
       wb.job[j] = wt_job(q.SL, q.mem + q.off_split, q.w.trip, t0, nt);
-      eb.job[j] = en_job(q.d, q.SL, q.mem + q.off_split, in, q.w, t0, nt);
+      if (e == cudaSuccess) e = en_job(&eb.job[j], q.d, q.SL, q.mem + q.off_split, in, q.w, t0, nt);
       total += take[j];
       cost += take[j] * q.cost_per_item;
     }
-    e = split_block_params(wb, eb, g + 1, ctx->num_sms, args, eargs, &kp, &ep);
+    if (e == cudaSuccess) e = split_block_params(wb, eb, g + 1, ctx->num_sms, args, eargs, &kp, &ep);
   }
   if (e != cudaSuccess) return false;
   if (!exec[g]) {

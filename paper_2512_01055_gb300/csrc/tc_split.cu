@@ -28,13 +28,14 @@
 // The FP32 accumulation along K rounds systematically, so L0 is restarted
 // every KCHAIN blocks (256 K values): the drain warps copy each finished chain
 // out of TMEM and add it into the tile's FP32 sum in shared memory; the last
-// chain also brings L1.  A finished tile leaves with one bulk store into the
-// job's W-term buffer Y[triplet][F][chunk][row][z].
+// chain also brings L1.  The drain writes a finished tile into the job's
+// W-term buffer in [a][b][c] orientation, Y[triplet][F][a][b][c], so that the
+// three F contributions to one W element sit at the same place.
 //
 // Energy kernel.  A work item is (triplet, chunk of tile orbits) as in the
-// FP64 path.  Per orbit it assembles the six 16^3 W blocks from the three F
-// buffers in shared memory and evaluates the Eq. 1 bracket at the orbit's
-// canonical points, writing one FP64 partial per item.
+// FP64 path.  Per orbit it sums the three F buffers' 16^3 boxes of each of the
+// six W blocks (TMA loads) in shared memory and evaluates the Eq. 1 bracket at
+// the orbit's canonical points, writing one FP64 partial per item.
 //
 // Operand images.  The slicer writes every operand block of 16 K values
 // directly in the tensor core's K-major no-swizzle layout (8-row x 16-byte
@@ -79,10 +80,19 @@ constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
 
 // energy kernel
-constexpr int EN_THREADS = 256;
+constexpr int EN_THREADS = 512;
+constexpr int EN_SLOTS = 2;               // staging slots of three 16^3 boxes
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
 constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
-constexpr int EN_SMEM = 6 * WBLK * 4;
+// V inputs of an orbit in shared memory: G_pq^uw = (p u|q w) for the three
+// occupied pairs (jk, ik, ij) and the six ordered pairs of the orbit's tile
+// positions (rows padded to 17), and t1 for the three occupied indices and
+// three tile positions
+constexpr int GROW = 17;
+constexpr int GV_FLOATS = 3 * 6 * NT * GROW;
+constexpr int T1_FLOATS = 3 * 3 * NT;
+constexpr int GV_LOADS = 3 * 6 * NT * NT + T1_FLOATS;
+constexpr int EN_SMEM = 1024 + 6 * WBLK * 4 + EN_SLOTS * 3 * 4096 * 4 + (GV_FLOATS + T1_FLOATS) * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -122,13 +132,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-               :: "l"(gdst), "r"(smem_u32(ssrc)), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows
 // x 16 bytes, the next core matrix along K 128 bytes on, the next 8-row group
@@ -408,8 +411,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
       const int ng = nc / 16, gsplit = (ng + 1) / 2;
       const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
       float *srow = sum + (size_t)lrow * ys + g0 * 16;
-      // the previous tile's bulk store has finished reading the sum tile
-      if (et == 0) bulk_wait_read();
+      // every thread has finished writing out the previous tile
       drain_bar();
       for (int ch = 0; ch < nchain; ++ch) {
         if (et == 0) drain_ok = mbar_wait(&accfull_bar, aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
@@ -454,17 +456,49 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         aphase ^= 1u;
       }
       if (!ok) break;
-      // the finished tile leaves with one bulk store
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // The finished tile goes to the W-term buffer of its F in [a][b][c]
+      // orientation: F(i,j,k)[ab,c] row-wise, F(i,k,j)[ac,b] and F(j,k,i)[bc,a]
+      // with the lanes on 32 consecutive rows (consecutive c) of one column.
       drain_bar();
-      if (et == 0) {
+      {
         int m, tl, g, nci;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
-        const size_t tile = (((size_t)tl * 3 + g) * J.g.nch + nci) * J.g.mt + m;
-        bulk_store(J.y + tile * MROWS * ys, sum, (uint32_t)(MROWS * ys * 4));
+        const int v = J.g.v, vc = J.g.vc;
+        const int vv = v * v, row0 = m * MROWS;
+        const int cbase = nci * nc;
+        float *Wf = J.y + (size_t)(tl * 3 + g) * vv * vc;
+        if (g == 0) {
+          const int nq = nc / 4;
+          for (int k = et; k < MROWS * nq; k += DRAIN_THREADS) {
+            const int r = k / nq, c4 = k - r * nq;
+            const int row = (int)row0 + r;                    // a v + b
+            const int z = cbase + 4 * c4;                     // c
+            if (row >= vv || z >= v) continue;
+            *(float4 *)(Wf + (size_t)row * vc + z) = *(const float4 *)(sum + (size_t)r * ys + 4 * c4);
+          }
+        } else {
+          // this lane's four rows (one per 32-row group): (p, c) = (row / v, row % v)
+          int pr[MROWS / 32], cr[MROWS / 32];
+#pragma unroll
+          for (int rg = 0; rg < MROWS / 32; ++rg) {
+            const int row = (int)row0 + rg * 32 + lane;
+            pr[rg] = row < vv ? row / v : -1;
+            cr[rg] = row - pr[rg] * v;
+          }
+          const int cend = min(nc, v - cbase);
+          for (int col = et >> 5; col < cend; col += DRAIN_THREADS / 32) {
+            const int z = cbase + col;
+#pragma unroll
+            for (int rg = 0; rg < MROWS / 32; ++rg) {
+              if (pr[rg] < 0) continue;
+              // g = 1: row (a, c), column b;  g = 2: row (b, c), column a
+              const int ab = (g == 1) ? pr[rg] * v + z : z * v + pr[rg];
+              Wf[(size_t)ab * vc + cr[rg]] = sum[(size_t)(rg * 32 + lane) * ys + col];
+            }
+          }
+        }
       }
     }
-    if (et == 0) bulk_wait_all();
   }
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -476,115 +510,218 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
 }
 
 // ---------------------------------------------------------------- energy kernel
+//
+// One CTA per SM walks its items (triplet, orbit chunk); every distinct W block
+// of an orbit is one "block load": three 16^3 boxes, one from each F buffer,
+// fetched by TMA (4-D tensor map over the job's W-term buffer, zero-filled
+// where an index reaches v) into a staging slot.  Thread 0 keeps a second
+// cursor two block loads ahead and issues them as slots free up, so the loads
+// of the next blocks (and of the next orbit) fly while the current block is
+// repacked and the orbit's energy is evaluated.
 
-__global__ void __launch_bounds__(EN_THREADS, 2)
+// Index of the ordered pair (u, w) of distinct tile positions:
+// (0,1) (1,0) (0,2) (2,0) (1,2) (2,1)
+__host__ __device__ constexpr int tpair(int u, int w) {
+  return (u == 0) ? (w == 1 ? 0 : 2) : (u == 1) ? (w == 0 ? 1 : 4) : (w == 0 ? 3 : 5);
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+               :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Position in the sequence of block loads of a CTA.
+struct ECur {
+  long long gi;        // global item
+  int jc;              // its job
+  int tl, ob, ob1;     // triplet in the block; current orbit; end of the item's orbits
+  int s;               // distinct block (formal permutation index) of the orbit
+  int tl3[3], blk[6];
+  bool valid;
+};
+
+__device__ __forceinline__ void ecur_orbit(const EnBatch &B, ECur &c) {
+  const int4 og = B.job[c.jc].orb[c.ob];
+  c.tl3[0] = og.x; c.tl3[1] = og.y; c.tl3[2] = og.z;
+  orbit_blocks(c.tl3, c.blk);
+  c.s = 0;                                           // the identity block is always distinct
+}
+__device__ __forceinline__ void ecur_item(const EnBatch &B, ECur &c) {
+  c.valid = c.gi < B.total_items;
+  if (!c.valid) return;
+  while (c.jc + 1 < B.njobs && c.gi >= B.job[c.jc + 1].item0) ++c.jc;
+  const EnJob &J = B.job[c.jc];
+  const long long q = c.gi - J.item0;
+  c.tl = (int)(q / J.d.items_per_trip);
+  const int chunk = (int)(q % J.d.items_per_trip);
+  c.ob = chunk * J.d.orb_per_item;
+  c.ob1 = min(J.d.n_orb, c.ob + J.d.orb_per_item);
+  ecur_orbit(B, c);
+}
+__device__ __forceinline__ void ecur_next(const EnBatch &B, ECur &c) {
+  while (++c.s < 6)
+    if (c.blk[c.s] == c.s) return;
+  if (++c.ob < c.ob1) { ecur_orbit(B, c); return; }
+  c.gi += gridDim.x;
+  ecur_item(B, c);
+}
+__device__ __forceinline__ bool ecur_last_of_orbit(const ECur &c) {
+  for (int s2 = c.s + 1; s2 < 6; ++s2)
+    if (c.blk[s2] == s2) return false;
+  return true;
+}
+
+// Issue the three boxes of block load c into staging slot dst (16 KB each):
+// the block (X, Y, Z) of F(i,j,k)[ab,c], F(i,k,j)[ac,b] and F(j,k,i)[bc,a],
+// all stored as [a][b][c]
+__device__ __forceinline__ void ecur_issue(const EnBatch &B, const ECur &c, float *dst, uint64_t *bar) {
+  const EnJob &J = B.job[c.jc];
+  const int X = c.tl3[perm3(c.s, 0)] * NT, Y = c.tl3[perm3(c.s, 1)] * NT, Z = c.tl3[perm3(c.s, 2)] * NT;
+  const int f0 = c.tl * 3;
+  mbar_expect_tx(bar, 3 * NT * NT * NT * 4);
+#pragma unroll
+  for (int g = 0; g < 3; ++g) tma_load_4d(dst + g * NT * NT * NT, &J.ymap, Z, Y, X, f0 + g, bar);
+}
+
+__global__ void __launch_bounds__(EN_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ EnBatch B) {
-  extern __shared__ __align__(16) float Wsm[];     // 6 W blocks
+  extern __shared__ __align__(1024) unsigned char en_raw[];
+  float *Wsm = (float *)(((uintptr_t)en_raw + 1023) & ~(uintptr_t)1023);   // 6 W blocks
+  float *stg = Wsm + 6 * WBLK;                                              // slots x 3 boxes
+  float *gsm = stg + EN_SLOTS * 3 * NT * NT * NT;                           // G tiles [3][6][16][17]
+  float *t1s = gsm + GV_FLOATS;                                             // t1 [3 occ][3 tiles][16]
+  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS];
   __shared__ double red[EN_THREADS / 32];
+  __shared__ int en_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int jc = 0;
-  for (long long gi = blockIdx.x; gi < B.total_items; gi += gridDim.x) {
-    while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
-    const EnJob &J = B.job[jc];
-    const Dims &d = J.d;
-    const SplitGeom &G = J.g;
-    const int o = d.o, v = d.v;
-    const long long q = gi - J.item0;
-    const int tl = (int)(q / d.items_per_trip), chunk = (int)(q % d.items_per_trip);
-    const int t = J.t0 + tl;
-    const int4 tr = J.trip[t];
-    const int occ[3] = {tr.x, tr.y, tr.z};
-    const double eijk = __ldg(J.eps + occ[0]) + __ldg(J.eps + occ[1]) + __ldg(J.eps + occ[2]);
-    // F buffer g of this triplet: rows (x, y) = x v + y, column z
-    const size_t fstride = (size_t)G.nch * G.mt * MROWS * G.ys;
-    const float *Yt = J.y + (size_t)tl * 3 * fstride;
-    double acc = 0.0;
-    const int ob1 = min(d.n_orb, (chunk + 1) * d.orb_per_item);
-    for (int ob = chunk * d.orb_per_item; ob < ob1; ++ob) {
-      const int4 og = J.orb[ob];
-      const int tl3[3] = {og.x, og.y, og.z};
-      int blk[6];
-      orbit_blocks(tl3, blk);
-      // W_abc = F(i,j,k)[ab,c] + F(i,k,j)[ac,b] + F(j,k,i)[bc,a]: one pass per F,
-      // 16-byte loads along the F's contiguous index (its column), the loads of
-      // three blocks in flight before their shared-memory writes.  Rows with an
-      // index >= v are 0; columns >= v read the W-term GEMM's zero padding.
-#pragma unroll 1
-      for (int pass = 0; pass < 3; ++pass) {
-        const float *Yg = Yt + pass * fstride;
-#pragma unroll 1
-        for (int s0 = 0; s0 < 6; s0 += 3) {
-          float4 val[3][4];
-#pragma unroll
-          for (int si = 0; si < 3; ++si) {
-            const int s = s0 + si;
-            const int X = tl3[perm3(s, 0)] * NT, Y = tl3[perm3(s, 1)] * NT, Z = tl3[perm3(s, 2)] * NT;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int f = tid + EN_THREADS * u;            // float4 index in the block, 0 .. 1023
-              const int hi = f >> 6, mid = (f >> 2) & 15, lo = (f & 3) * 4;
-              int r0, r1, col;                               // row = r0 * v + r1
-              if (pass == 0)      { r0 = X + hi; r1 = Y + mid; col = Z + lo; }
-              else if (pass == 1) { r0 = X + hi; r1 = Z + mid; col = Y + lo; }
-              else                { r0 = Y + hi; r1 = Z + mid; col = X + lo; }
-              float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (blk[s] == s && r0 < v && r1 < v) {
-                const int nci = col / G.nc;
-                x = __ldg((const float4 *)(Yg + ((size_t)nci * G.mt * MROWS + (size_t)r0 * v + r1) * G.ys +
-                                           (col - nci * G.nc)));
-              }
-              val[si][u] = x;
-            }
-          }
-#pragma unroll
-          for (int si = 0; si < 3; ++si) {
-            const int s = s0 + si;
-            if (blk[s] != s) continue;
-            float *Wb = Wsm + s * WBLK;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int f = tid + EN_THREADS * u;
-              const int hi = f >> 6, mid = (f >> 2) & 15, lo = (f & 3) * 4;
-              // the four points of the load differ in the F's column index
-              float *w;
-              int step;
-              if (pass == 0)      { w = Wb + hi * WX + mid * WY + lo; step = 1; }
-              else if (pass == 1) { w = Wb + hi * WX + lo * WY + mid; step = WY; }
-              else                { w = Wb + lo * WX + hi * WY + mid; step = WX; }
-              const float4 x = val[si][u];
-              if (pass == 0) {
-                w[0] = x.x; w[step] = x.y; w[2 * step] = x.z; w[3 * step] = x.w;
-              } else {
-                w[0] += x.x; w[step] += x.y; w[2 * step] += x.z; w[3 * step] += x.w;
-              }
-            }
-          }
-        }
-        __syncthreads();
-      }
+  constexpr int BOXF = NT * NT * NT;
 
-      // energy over the canonical points a >= b >= c of the orbit
-      for (int pr = tid; pr < NT * NT; pr += EN_THREADS) {
-        const int la = pr >> 4, lb = pr & 15;
-        const int ga = tl3[0] * NT + la, gb = tl3[1] * NT + lb;
-        if (ga >= v || gb >= v || ga < gb) continue;
+  if (tid == 0) {
+    for (int k = 0; k < EN_SLOTS; ++k) mbar_init(&full_bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    en_ok = 1;
+  }
+  __syncthreads();
+
+  ECur cc{};
+  cc.gi = blockIdx.x;
+  cc.jc = 0;
+  ecur_item(B, cc);
+  ECur pc = cc;                                      // producer cursor (used by thread 0)
+  long long issued = 0;
+  if (tid == 0) {
+    for (int k = 0; k < EN_SLOTS && pc.valid; ++k) {
+      ecur_issue(B, pc, stg + (size_t)k * 3 * BOXF, &full_bar[k]);
+      ++issued;
+      ecur_next(B, pc);
+    }
+  }
+  double acc = 0.0;
+  long long seq = 0;
+  while (cc.valid) {
+    const EnJob &J = B.job[cc.jc];
+    const Dims &d = J.d;
+    const int o = d.o, v = d.v;
+    const int slot = (int)(seq % EN_SLOTS);
+    const uint32_t par = (uint32_t)((seq / EN_SLOTS) & 1);
+    const int4 tr = J.trip[J.t0 + cc.tl];
+    const int occ[3] = {tr.x, tr.y, tr.z};
+    // an orbit's first block: load its V inputs (stored below, read by the compute)
+    constexpr int GV_PER = (GV_LOADS + EN_THREADS - 1) / EN_THREADS;
+    float gv[GV_PER];
+    const bool first_block = cc.s == 0;
+    if (first_block) {
+#pragma unroll
+      for (int q = 0; q < GV_PER; ++q) {
+        const int idx = tid + EN_THREADS * q;
+        float val = 0.f;
+        if (idx < 3 * 6 * NT * NT) {
+          const int op = idx / (6 * NT * NT), tp = (idx / (NT * NT)) % 6, u = (idx >> 4) & 15, w = idx & 15;
+          const int pu = (tp < 2) ? tp : (tp < 4 ? (tp == 2 ? 0 : 2) : (tp == 4 ? 1 : 2));
+          const int pw = (tp == 0) ? 1 : (tp == 1 ? 0 : (tp == 2 ? 2 : (tp == 3 ? 0 : (tp == 4 ? 2 : 1))));
+          const int U = cc.tl3[pu] * NT + u, Wc = cc.tl3[pw] * NT + w;
+          const int p0 = op == 0 ? occ[1] : occ[0], q0 = op == 2 ? occ[1] : occ[2];
+          if (U < v && Wc < v) val = __ldg(J.ovovf + (((size_t)p0 * v + U) * o + q0) * v + Wc);
+        } else if (idx < GV_LOADS) {
+          const int e2 = idx - 3 * 6 * NT * NT;
+          const int op = e2 / (3 * NT), tp = (e2 / NT) % 3, l = e2 % NT;
+          const int a = cc.tl3[tp] * NT + l;
+          if (a < v) val = __ldg(J.t1f + occ[op] * v + a);
+        }
+        gv[q] = val;
+      }
+    }
+    // wait for the block's boxes (bounded)
+    {
+      const uint32_t a = smem_u32(&full_bar[slot]);
+      long long it = 0;
+      while (!mbar_try(a, par)) {
+        if (++it == WAIT_LIMIT) { if (tid == 0) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_FULL); } break; }
+        if ((it & 255) == 255) __nanosleep(64);
+      }
+    }
+    __syncthreads();
+    if (!en_ok) break;
+    // W = box 0 + box 1 + box 2 into the padded W block
+    {
+      const float4 *sb = (const float4 *)(stg + (size_t)slot * 3 * BOXF);
+      float *Wb = Wsm + cc.s * WBLK;
+#pragma unroll
+      for (int k = 0; k < BOXF / 4 / EN_THREADS; ++k) {
+        const int e4 = tid + k * EN_THREADS;              // float4 index: (x, y, z4)
+        const float4 a0 = sb[e4], a1 = sb[BOXF / 4 + e4], a2 = sb[2 * BOXF / 4 + e4];
+        const int x = e4 >> 6, y = (e4 >> 2) & 15, z = (e4 & 3) * 4;
+        float *w = Wb + x * WX + y * WY + z;
+        w[0] = a0.x + a1.x + a2.x;
+        w[1] = a0.y + a1.y + a2.y;
+        w[2] = a0.z + a1.z + a2.z;
+        w[3] = a0.w + a1.w + a2.w;
+      }
+      if (first_block) {
+#pragma unroll
+        for (int q = 0; q < GV_PER; ++q) {
+          const int idx = tid + EN_THREADS * q;
+          if (idx < 3 * 6 * NT * NT) gsm[(idx >> 4) * GROW + (idx & 15)] = gv[q];
+          else if (idx < GV_LOADS) t1s[idx - 3 * 6 * NT * NT] = gv[q];
+        }
+      }
+    }
+    __syncthreads();
+    // the slot is free: the producer refills it with the load two ahead
+    if (tid == 0 && pc.valid) {
+      ecur_issue(B, pc, stg + (size_t)slot * 3 * BOXF, &full_bar[slot]);
+      ++issued;
+      ecur_next(B, pc);
+    }
+    const bool orbit_done = ecur_last_of_orbit(cc);
+    if (orbit_done) {
+      // energy over the canonical points a >= b >= c of the orbit; threads
+      // (pr, half) take point row (la, lb) and half of its lc range
+      const double eijk = __ldg(J.eps + occ[0]) + __ldg(J.eps + occ[1]) + __ldg(J.eps + occ[2]);
+      const int pr = tid & (NT * NT - 1), hf = tid >> 8;
+      const int la = pr >> 4, lb = pr & 15;
+      const int ga = cc.tl3[0] * NT + la, gb = cc.tl3[1] * NT + lb;
+      if (ga < v && gb < v && ga >= gb) {
         const double dab = eijk - (__ldg(J.eps + o + ga) + __ldg(J.eps + o + gb));
-        float rowsum = 0.f;                // the row's up to 16 points, added into acc in FP64 once
-        for (int lcc = 0; lcc < NT; ++lcc) {
-          const int gc = tl3[2] * NT + lcc;
+        float rowsum = 0.f;                  // up to 8 points, added into acc in FP64 once
+        for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
+          const int gc = cc.tl3[2] * NT + lcc;
           if (gc >= v || gb < gc) continue;
           const int l3[3] = {la, lb, lcc};
-          const int g3[3] = {ga, gb, gc};
           float ws[6], vs[6];
 #pragma unroll
           for (int s = 0; s < 6; ++s) {
             const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
-            ws[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
-            const int x = g3[p0], y = g3[p1], z = g3[p2];
-            const float *ov = J.ovovf;
-            vs[s] = __ldg(J.t1f + occ[0] * v + x) * __ldg(ov + ((occ[1] * v + y) * o + occ[2]) * v + z)
-                  + __ldg(J.t1f + occ[1] * v + y) * __ldg(ov + ((occ[0] * v + x) * o + occ[2]) * v + z)
-                  + __ldg(J.t1f + occ[2] * v + z) * __ldg(ov + ((occ[0] * v + x) * o + occ[1]) * v + y);
+            ws[s] = Wsm[cc.blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
+            // V (Eq. 3) at (x, y, z) = positions (p0, p1, p2) of the point:
+            // t_i^x G_jk^yz + t_j^y G_ik^xz + t_k^z G_ij^xy
+            const int x = l3[p0], y = l3[p1], z = l3[p2];
+            vs[s] = t1s[(0 * 3 + p0) * NT + x] * gsm[((0 * 6 + tpair(p1, p2)) * NT + y) * GROW + z]
+                  + t1s[(1 * 3 + p1) * NT + y] * gsm[((1 * 6 + tpair(p0, p2)) * NT + x) * GROW + z]
+                  + t1s[(2 * 3 + p2) * NT + z] * gsm[((2 * 6 + tpair(p0, p1)) * NT + x) * GROW + y];
           }
           const float se = ws[0] + ws[3] + ws[4];
           const float so = ws[1] + ws[2] + ws[5];
@@ -602,21 +739,40 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         }
         acc += (double)rowsum;
       }
-      __syncthreads();                    // W is rebuilt by the next orbit
+      __syncthreads();                       // W is rebuilt by the next orbit
     }
-    // the item's partial: fixed-order reduction over the block
+    // next block load; an item ends when the cursor leaves it
+    const long long gi_now = cc.gi;
+    const int t_now = J.t0 + cc.tl;
+    const long long slot_now = (long long)t_now * d.items_per_trip + (cc.gi - J.item0) % d.items_per_trip;
+    double *partial = J.partial;
+    ecur_next(B, cc);
+    ++seq;
+    if (!cc.valid || cc.gi != gi_now) {
+      // the item's partial: fixed-order reduction over the block
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) red[warp] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
 #pragma unroll
-      for (int wq = 0; wq < EN_THREADS / 32; ++wq) tot += red[wq];
-      J.partial[(long long)t * d.items_per_trip + chunk] = tot;
+        for (int wq = 0; wq < EN_THREADS / 32; ++wq) tot += red[wq];
+        partial[slot_now] = tot;
+      }
+      __syncthreads();
+      acc = 0.0;
     }
-    __syncthreads();
   }
+  // after an abort: the loads still in flight land before the CTA exits (bounded)
+  if (tid == 0) {
+    for (long long k = seq; k < issued; ++k) {
+      const uint32_t a = smem_u32(&full_bar[k % EN_SLOTS]);
+      for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k / EN_SLOTS) & 1)); ++it)
+        if ((it & 255) == 255) __nanosleep(128);
+    }
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- operand images
@@ -767,7 +923,7 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
   }
   eb.total_items = etotal;
   *wgrid = (int)std::max<long long>(1, std::min<long long>(num_sms, total));
-  *egrid = (int)std::max<long long>(1, std::min<long long>(2LL * num_sms, etotal));
+  *egrid = (int)std::max<long long>(1, std::min<long long>(num_sms, etotal));
   cudaError_t e = cudaSuccess;
   switch (S) {
     case 2: e = cudaFuncSetAttribute(tc_wterm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
@@ -794,6 +950,7 @@ SplitGeom split_geom(int o, int v, int S) {
   g.nch = (vp + NCMAX - 1) / NCMAX;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
   g.ys = g.nc + 4;
+  g.vc = (v + 3) / 4 * 4;
   // Triplets per block: about 16 W-term items per SM of a 152-SM GPU, at most
   // 64 and at most the number of triplets.
   const long long per_trip = 3LL * g.mt * g.nch;
@@ -820,7 +977,7 @@ SplitLayout split_layout(int o, int v, int S) {
   L.hb = take(b_o);
   L.t1f = take((size_t)o * v * 4);
   L.ovovf = take((size_t)o * v * o * v * 4);
-  L.y = take((size_t)g.nb * 3 * g.nch * g.mt * MROWS * g.ys * 4);
+  L.y = take((size_t)g.nb * 3 * v * v * g.vc * 4);
   L.total = off;
   return L;
 }
@@ -859,9 +1016,28 @@ WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int
   return J;
 }
 
-EnJob en_job(const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w, int t0, int nt) {
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return (EncodeTiled)p;
+  }();
+  return fn;
+}
+}  // namespace
+
+cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w,
+                   int t0, int nt) {
   const unsigned char *b = (const unsigned char *)ws;
-  EnJob J{};
+  EnJob &J = *out;
+  J = EnJob{};
   J.d = d;
   J.g = L.g;
   J.trip = w.trip;
@@ -873,7 +1049,20 @@ EnJob en_job(const Dims &d, const SplitLayout &L, const void *ws, const Inputs &
   J.partial = w.partial;
   J.t0 = t0;
   J.nt = nt;
-  return J;
+  // W-term buffer [nt][3][a][b][vc] as (c < v, b < v, a < v, 3 t + F): boxes of
+  // 16^3, zero-filled where an index reaches v
+  const SplitGeom &g = L.g;
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t rowb = (cuuint64_t)g.vc * 4;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)3 * nt};
+  const cuuint64_t strides[3] = {rowb, rowb * g.v, rowb * g.v * g.v};
+  const cuuint32_t box[4] = {NT, NT, NT, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(&J.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)J.y, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t split_block_params(WtBatch &wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,

@@ -88,6 +88,9 @@ def test_admission_by_hbm_footprint():
     ctx = tc.tc_init(0, hbm_budget_bytes=int(1.5 * one), max_inflight=8, iteration_ms=5)
     try:
         ref = [alone(j, p, s) for (j, p, s) in jobs]
+        # hold the scheduler so the first admitted job keeps its memory while
+        # the others are submitted (each job alone finishes in milliseconds)
+        assert tc.tc_inject_fault(ctx, tc.TC_FAULT_STALL, 500) == tc.TC_OK
         tickets = submit_all(ctx, jobs)
         seen_queue = False
         for _ in range(200):
