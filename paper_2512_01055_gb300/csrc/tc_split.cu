@@ -26,11 +26,12 @@
 // Per K block of 16 the MMA warp issues one MMA per slice pair: level 0 into
 // accumulator L0, levels >= 1 into L1 (TMEM columns [0, nc) and [nc, 2nc)).
 // The FP32 accumulation along K rounds systematically, so L0 is restarted
-// every KCHAIN blocks (256 K values): the drain warps copy each finished chain
-// out of TMEM and add it into the tile's FP32 sum in shared memory; the last
-// chain also brings L1.  The drain writes a finished tile into the job's
-// W-term buffer in [a][b][c] orientation, Y[triplet][F][a][b][c], so that the
-// three F contributions to one W element sit at the same place.
+// every KCHAIN blocks (256 K values): the drain warps (a thread holds one tile
+// row) copy each finished chain out of TMEM and add it into the row's FP32 sum
+// in shared memory; on the last chain they add L1 and the earlier chains' sum
+// and write the row into the job's W-term buffer in [a][b][c] orientation,
+// Y[triplet][F][a][b][c], so that the three F contributions to one W element
+// sit at the same place.
 //
 // Energy kernel.  A work item is (triplet, chunk of tile orbits) as in the
 // FP64 path.  Per orbit it sums the three F buffers' 16^3 boxes of each of the
@@ -410,16 +411,14 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
       const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
       const int ng = nc / 16, gsplit = (ng + 1) / 2;
       const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
-      float *srow = sum + (size_t)lrow * ys + g0 * 16;
-      // every thread has finished writing out the previous tile
-      drain_bar();
+      float *srow = sum + (size_t)lrow * ys + g0 * 16;   // this thread's row of the tile sum
       for (int ch = 0; ch < nchain; ++ch) {
         if (et == 0) drain_ok = mbar_wait(&accfull_bar, aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
         drain_bar();
         if (!drain_ok) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // Read the chain's L0 (and on the last chain add L1) into registers,
-        // hand the accumulators back to the MMA warp, then add into the sum.
+        // Read the chain's L0 (and on the last chain add L1) into registers and
+        // hand the accumulators back to the MMA warp.
         float v[MAXG][16];
 #pragma unroll
         for (int gi2 = 0; gi2 < MAXG; ++gi2)
@@ -439,65 +438,74 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         drain_bar();
         if (et == 0) mbar_arrive(&accempty_bar);
+        aphase ^= 1u;
+        if (ch + 1 < nchain) {
+          // an intermediate chain: into this thread's row of the tile sum
 #pragma unroll
-        for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-          if (gi2 >= my) break;
-          float4 *d4 = (float4 *)(srow + gi2 * 16);
+          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+            if (gi2 >= my) break;
+            float4 *d4 = (float4 *)(srow + gi2 * 16);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float4 x = make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
-            if (ch > 0) {
-              const float4 s0 = d4[e];
-              x.x += s0.x; x.y += s0.y; x.z += s0.z; x.w += s0.w;
+            for (int e = 0; e < 4; ++e) {
+              float4 x = make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
+              if (ch > 0) {
+                const float4 s0 = d4[e];
+                x.x += s0.x; x.y += s0.y; x.z += s0.z; x.w += s0.w;
+              }
+              d4[e] = x;
             }
-            d4[e] = x;
+          }
+          continue;
+        }
+        // The last chain: add the earlier chains' sum of this row and store the
+        // row into the W-term buffer of its F in [a][b][c] orientation.  For
+        // F(i,k,j)[ac,b] and F(j,k,i)[bc,a] the warp's 32 lanes hold 32
+        // consecutive c, so the stores column by column are 128-byte coalesced.
+        if (ch > 0) {
+#pragma unroll
+          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+            if (gi2 >= my) break;
+            const float4 *d4 = (const float4 *)(srow + gi2 * 16);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float4 s0 = d4[e];
+              v[gi2][4 * e] += s0.x; v[gi2][4 * e + 1] += s0.y; v[gi2][4 * e + 2] += s0.z; v[gi2][4 * e + 3] += s0.w;
+            }
           }
         }
-        aphase ^= 1u;
-      }
-      if (!ok) break;
-      // The finished tile goes to the W-term buffer of its F in [a][b][c]
-      // orientation: F(i,j,k)[ab,c] row-wise, F(i,k,j)[ac,b] and F(j,k,i)[bc,a]
-      // with the lanes on 32 consecutive rows (consecutive c) of one column.
-      drain_bar();
-      {
         int m, tl, g, nci;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
-        const int v = J.g.v, vc = J.g.vc;
-        const int vv = v * v, row0 = m * MROWS;
-        const int cbase = nci * nc;
-        float *Wf = J.y + (size_t)(tl * 3 + g) * vv * vc;
-        if (g == 0) {
-          const int nq = nc / 4;
-          for (int k = et; k < MROWS * nq; k += DRAIN_THREADS) {
-            const int r = k / nq, c4 = k - r * nq;
-            const int row = (int)row0 + r;                    // a v + b
-            const int z = cbase + 4 * c4;                     // c
-            if (row >= vv || z >= v) continue;
-            *(float4 *)(Wf + (size_t)row * vc + z) = *(const float4 *)(sum + (size_t)r * ys + 4 * c4);
-          }
-        } else {
-          // this lane's four rows (one per 32-row group): (p, c) = (row / v, row % v)
-          int pr[MROWS / 32], cr[MROWS / 32];
+        const int vo = J.g.v, vc = J.g.vc;
+        const int row = m * MROWS + lrow;
+        if (row < vo * vo) {
+          const int zb = nci * nc + g0 * 16;
+          float *Wf = J.y + (size_t)(tl * 3 + g) * vo * vo * vc;
+          if (g == 0) {                                  // row (a, b), columns c
+            float *dst = Wf + (size_t)row * vc + zb;
 #pragma unroll
-          for (int rg = 0; rg < MROWS / 32; ++rg) {
-            const int row = (int)row0 + rg * 32 + lane;
-            pr[rg] = row < vv ? row / v : -1;
-            cr[rg] = row - pr[rg] * v;
-          }
-          const int cend = min(nc, v - cbase);
-          for (int col = et >> 5; col < cend; col += DRAIN_THREADS / 32) {
-            const int z = cbase + col;
+            for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+              if (gi2 >= my) break;
 #pragma unroll
-            for (int rg = 0; rg < MROWS / 32; ++rg) {
-              if (pr[rg] < 0) continue;
-              // g = 1: row (a, c), column b;  g = 2: row (b, c), column a
-              const int ab = (g == 1) ? pr[rg] * v + z : z * v + pr[rg];
-              Wf[(size_t)ab * vc + cr[rg]] = sum[(size_t)(rg * 32 + lane) * ys + col];
+              for (int e = 0; e < 4; ++e)
+                if (zb + gi2 * 16 + 4 * e < vo)
+                  *(float4 *)(dst + gi2 * 16 + 4 * e) =
+                      make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
+            }
+          } else {                                       // row (p, c); column b (g = 1) or a (g = 2)
+            const int p = row / vo, c = row - p * vo;
+            const size_t st = (g == 1) ? (size_t)vc : (size_t)vo * vc;
+            float *dst = Wf + ((g == 1) ? (size_t)p * vo * vc : (size_t)p * vc) + c + (size_t)zb * st;
+#pragma unroll
+            for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+              if (gi2 >= my) break;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (zb + gi2 * 16 + e < vo) dst[(size_t)(gi2 * 16 + e) * st] = v[gi2][e];
             }
           }
         }
       }
+      if (!ok) break;
     }
   }
 
