@@ -90,7 +90,6 @@ struct SplitGeom {
   int mt;                // M tiles: ceil(v^2 / 128)
   int kbv, kbo;          // K blocks over a virtual / an occupied index
   int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
-  int ys;                // row stride of a W-term tile in shared memory, floats (nc + 4)
   int vc;                // innermost extent of the W-term buffer (v rounded up to 4)
   int nb;                // triplets per block (capacity of the W-term buffer)
 };
@@ -98,7 +97,7 @@ struct SplitGeom {
 // job's split workspace.
 struct SplitLayout {
   SplitGeom g;
-  size_t pa, pa2, hc, hc2, tb, hb, t1f, ovovf, y;
+  size_t pa, pa2, hc, hc2, tb, hb, t1f, epsf, ovovf, y;
   size_t total;
 };
 struct WtJob {           // one job's block of triplets in a W-term launch
@@ -112,7 +111,7 @@ struct WtJob {           // one job's block of triplets in a W-term launch
 struct WtBatch {
   int njobs;
   int stages, nprod;     // set by the launcher
-  size_t slot, sum_off;  // set by the launcher: stage stride and tile-sum offset in shared memory
+  size_t slot;           // set by the launcher: stage stride in shared memory
   long long total_items;
   int *err;
   WtJob job[MAX_BATCH];
@@ -123,7 +122,7 @@ struct EnJob {           // one job's block of triplets in an energy launch
   SplitGeom g;
   const int4 *trip, *orb;
   const double *eps;
-  const float *t1f, *ovovf, *y;
+  const float *t1f, *epsf, *ovovf, *y;
   double *partial;       // [n_items], slot t * items_per_trip + chunk
   int t0, nt;
   long long item0;

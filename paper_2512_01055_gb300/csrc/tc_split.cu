@@ -27,11 +27,11 @@
 // accumulator L0, levels >= 1 into L1 (TMEM columns [0, nc) and [nc, 2nc)).
 // The FP32 accumulation along K rounds systematically, so L0 is restarted
 // every KCHAIN blocks (256 K values): the drain warps (a thread holds one tile
-// row) copy each finished chain out of TMEM and add it into the row's FP32 sum
-// in shared memory; on the last chain they add L1 and the earlier chains' sum
-// and write the row into the job's W-term buffer in [a][b][c] orientation,
-// Y[triplet][F][a][b][c], so that the three F contributions to one W element
-// sit at the same place.
+// row, half its columns) add each finished chain into the row's FP32 sum in
+// registers; on the last chain they add L1 and write the row into the job's
+// W-term buffer in [a][b][c] orientation, Y[triplet][F][a][b][c], so that the
+// three F contributions to one W element sit at the same place.  Shared memory
+// holds only the operand pipeline.
 //
 // Energy kernel.  A work item is (triplet, chunk of tile orbits) as in the
 // FP64 path.  Per orbit it sums the three F buffers' 16^3 boxes of each of the
@@ -241,7 +241,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 tc_wterm_kernel(const __grid_constant__ WtBatch B) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float *sum = (float *)(sm + B.sum_off);       // the tile's FP32 sum [128][ys]
 
   __shared__ __align__(8) uint64_t full_bar[MAX_STAGES], empty_bar[MAX_STAGES];
   __shared__ __align__(8) uint64_t accfull_bar, accempty_bar, teardown_bar;
@@ -394,7 +393,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
     }
     __syncwarp();
   } else {
-    // ------------------------------------------------------------ drain: TMEM -> tile sum -> Y
+    // ------------------------------------------------------------ drain: TMEM -> row sums in registers -> Y
     const int et = tid - 64;                        // 0 .. 255
     const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;               // which half of the 16-column groups
@@ -406,73 +405,51 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
     for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
       while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
       const WtJob &J = B.job[jc];
-      const int nc = J.g.nc, ys = J.g.ys;
+      const int nc = J.g.nc;
       const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
       const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
       const int ng = nc / 16, gsplit = (ng + 1) / 2;
       const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
-      float *srow = sum + (size_t)lrow * ys + g0 * 16;   // this thread's row of the tile sum
+      float v[MAXG][16];                              // this thread's row: running sum over chains
       for (int ch = 0; ch < nchain; ++ch) {
         if (et == 0) drain_ok = mbar_wait(&accfull_bar, aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
         drain_bar();
         if (!drain_ok) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // Read the chain's L0 (and on the last chain add L1) into registers and
-        // hand the accumulators back to the MMA warp.
-        float v[MAXG][16];
+        // The row's running sum lives in v: the first chain's L0 is read into
+        // it, later chains add theirs (and the last chain L1 as well) one
+        // 16-column group at a time; then the accumulators go back to the MMA
+        // warp.
+        const bool last = ch + 1 == nchain;
+        if (ch == 0 && !last) {
 #pragma unroll
-        for (int gi2 = 0; gi2 < MAXG; ++gi2)
-          if (gi2 < my) tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), v[gi2]);
-        tmem_wait_ld();
-        if (ch + 1 == nchain) {
+          for (int gi2 = 0; gi2 < MAXG; ++gi2)
+            if (gi2 < my) tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), v[gi2]);
+          tmem_wait_ld();
+        } else {
 #pragma unroll
           for (int gi2 = 0; gi2 < MAXG; ++gi2) {
             if (gi2 >= my) break;
-            float l1[16];
-            tmem_ld16(trow + (uint32_t)(nc + (g0 + gi2) * 16), l1);
+            float l0[16], l1[16];
+            tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), l0);
+            if (last) tmem_ld16(trow + (uint32_t)(nc + (g0 + gi2) * 16), l1);
             tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 16; ++e) v[gi2][e] += l1[e];
+            for (int e = 0; e < 16; ++e) {
+              const float x = last ? l0[e] + l1[e] : l0[e];
+              v[gi2][e] = ch > 0 ? x + v[gi2][e] : x;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         drain_bar();
         if (et == 0) mbar_arrive(&accempty_bar);
         aphase ^= 1u;
-        if (ch + 1 < nchain) {
-          // an intermediate chain: into this thread's row of the tile sum
-#pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-            if (gi2 >= my) break;
-            float4 *d4 = (float4 *)(srow + gi2 * 16);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              float4 x = make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
-              if (ch > 0) {
-                const float4 s0 = d4[e];
-                x.x += s0.x; x.y += s0.y; x.z += s0.z; x.w += s0.w;
-              }
-              d4[e] = x;
-            }
-          }
-          continue;
-        }
-        // The last chain: add the earlier chains' sum of this row and store the
-        // row into the W-term buffer of its F in [a][b][c] orientation.  For
-        // F(i,k,j)[ac,b] and F(j,k,i)[bc,a] the warp's 32 lanes hold 32
-        // consecutive c, so the stores column by column are 128-byte coalesced.
-        if (ch > 0) {
-#pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-            if (gi2 >= my) break;
-            const float4 *d4 = (const float4 *)(srow + gi2 * 16);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float4 s0 = d4[e];
-              v[gi2][4 * e] += s0.x; v[gi2][4 * e + 1] += s0.y; v[gi2][4 * e + 2] += s0.z; v[gi2][4 * e + 3] += s0.w;
-            }
-          }
-        }
+        if (!last) continue;
+        // The last chain: store the row into the W-term buffer of its F in
+        // [a][b][c] orientation.  For F(i,k,j)[ac,b] and F(j,k,i)[bc,a] the warp's
+        // 32 lanes hold 32 consecutive c, so the stores column by column are
+        // 128-byte coalesced.
         int m, tl, g, nci;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
         const int vo = J.g.v, vc = J.g.vc;
@@ -551,9 +528,7 @@ struct ECur {
   bool valid;
 };
 
-__device__ __forceinline__ void ecur_orbit(const EnBatch &B, ECur &c) {
-  const int4 og = B.job[c.jc].orb[c.ob];
-  c.tl3[0] = og.x; c.tl3[1] = og.y; c.tl3[2] = og.z;
+__device__ __forceinline__ void ecur_orbit(ECur &c) {
   orbit_blocks(c.tl3, c.blk);
   c.s = 0;                                           // the identity block is always distinct
 }
@@ -567,12 +542,21 @@ __device__ __forceinline__ void ecur_item(const EnBatch &B, ECur &c) {
   const int chunk = (int)(q % J.d.items_per_trip);
   c.ob = chunk * J.d.orb_per_item;
   c.ob1 = min(J.d.n_orb, c.ob + J.d.orb_per_item);
-  ecur_orbit(B, c);
+  const int4 og = J.orb[c.ob];                       // the item's first orbit; the next ones follow
+  c.tl3[0] = og.x; c.tl3[1] = og.y; c.tl3[2] = og.z;
+  ecur_orbit(c);
 }
 __device__ __forceinline__ void ecur_next(const EnBatch &B, ECur &c) {
   while (++c.s < 6)
     if (c.blk[c.s] == c.s) return;
-  if (++c.ob < c.ob1) { ecur_orbit(B, c); return; }
+  if (++c.ob < c.ob1) {
+    // the orbit table's order, P >= Q >= R lexicographic, as an odometer
+    if (c.tl3[2] < c.tl3[1]) ++c.tl3[2];
+    else if (c.tl3[1] < c.tl3[0]) { ++c.tl3[1]; c.tl3[2] = 0; }
+    else { ++c.tl3[0]; c.tl3[1] = 0; c.tl3[2] = 0; }
+    ecur_orbit(c);
+    return;
+  }
   c.gi += gridDim.x;
   ecur_item(B, c);
 }
@@ -662,17 +646,16 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         gv[q] = val;
       }
     }
-    // wait for the block's boxes (bounded)
+    // wait for the block's boxes (bounded; a thread that gives up clears en_ok,
+    // which every thread reads after the barrier that ends the repack)
     {
       const uint32_t a = smem_u32(&full_bar[slot]);
       long long it = 0;
       while (!mbar_try(a, par)) {
-        if (++it == WAIT_LIMIT) { if (tid == 0) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_FULL); } break; }
+        if (++it == WAIT_LIMIT) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_FULL); break; }
         if ((it & 255) == 255) __nanosleep(64);
       }
     }
-    __syncthreads();
-    if (!en_ok) break;
     // W = box 0 + box 1 + box 2 into the padded W block
     {
       const float4 *sb = (const float4 *)(stg + (size_t)slot * 3 * BOXF);
@@ -698,6 +681,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
       }
     }
     __syncthreads();
+    if (!en_ok) break;
     // the slot is free: the producer refills it with the load two ahead
     if (tid == 0 && pc.valid) {
       ecur_issue(B, pc, stg + (size_t)slot * 3 * BOXF, &full_bar[slot]);
@@ -713,12 +697,42 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
       const int la = pr >> 4, lb = pr & 15;
       const int ga = cc.tl3[0] * NT + la, gb = cc.tl3[1] * NT + lb;
       if (ga < v && gb < v && ga >= gb) {
-        const double dab = eijk - (__ldg(J.eps + o + ga) + __ldg(J.eps + o + gb));
+        // D = e_i + e_j + e_k - e_a - e_b - e_c: the row's part in FP64, then
+        // per point in FP32 (all terms of D share a sign for canonical orbital
+        // energies, |D| > 1, so no cancellation is lost)
+        const float dab = (float)(eijk - (__ldg(J.eps + o + ga) + __ldg(J.eps + o + gb)));
+        // V inputs of the row that do not depend on c: t1 at the a and b
+        // positions, G at the position pairs (a, b) and (b, a); per op
+        // 0, 1, 2 = occupied pair (j, k), (i, k), (i, j) for G and i, j, k for t1
+        float ta[3], tb[3], gab[3], gba[3];
+#pragma unroll
+        for (int op = 0; op < 3; ++op) {
+          ta[op] = t1s[(op * 3 + 0) * NT + la];
+          tb[op] = t1s[(op * 3 + 1) * NT + lb];
+          gab[op] = gsm[((op * 6 + tpair(0, 1)) * NT + la) * GROW + lb];
+          gba[op] = gsm[((op * 6 + tpair(1, 0)) * NT + lb) * GROW + la];
+        }
         float rowsum = 0.f;                  // up to 8 points, added into acc in FP64 once
         for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
           const int gc = cc.tl3[2] * NT + lcc;
           if (gc >= v || gb < gc) continue;
           const int l3[3] = {la, lb, lcc};
+          float tcc[3], gac[3], gca[3], gbc[3], gcb[3];
+#pragma unroll
+          for (int op = 0; op < 3; ++op) {
+            tcc[op] = t1s[(op * 3 + 2) * NT + lcc];
+            gac[op] = gsm[((op * 6 + tpair(0, 2)) * NT + la) * GROW + lcc];
+            gca[op] = gsm[((op * 6 + tpair(2, 0)) * NT + lcc) * GROW + la];
+            gbc[op] = gsm[((op * 6 + tpair(1, 2)) * NT + lb) * GROW + lcc];
+            gcb[op] = gsm[((op * 6 + tpair(2, 1)) * NT + lcc) * GROW + lb];
+          }
+          // t1 of op at position pos, G of op at positions (pu, pw)
+          auto tv = [&](int op, int pos) { return pos == 0 ? ta[op] : (pos == 1 ? tb[op] : tcc[op]); };
+          auto gv = [&](int op, int pu, int pw) {
+            return pu == 0 ? (pw == 1 ? gab[op] : gac[op])
+                 : pu == 1 ? (pw == 0 ? gba[op] : gbc[op])
+                           : (pw == 0 ? gca[op] : gcb[op]);
+          };
           float ws[6], vs[6];
 #pragma unroll
           for (int s = 0; s < 6; ++s) {
@@ -726,10 +740,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
             ws[s] = Wsm[cc.blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
             // V (Eq. 3) at (x, y, z) = positions (p0, p1, p2) of the point:
             // t_i^x G_jk^yz + t_j^y G_ik^xz + t_k^z G_ij^xy
-            const int x = l3[p0], y = l3[p1], z = l3[p2];
-            vs[s] = t1s[(0 * 3 + p0) * NT + x] * gsm[((0 * 6 + tpair(p1, p2)) * NT + y) * GROW + z]
-                  + t1s[(1 * 3 + p1) * NT + y] * gsm[((1 * 6 + tpair(p0, p2)) * NT + x) * GROW + z]
-                  + t1s[(2 * 3 + p2) * NT + z] * gsm[((2 * 6 + tpair(p0, p1)) * NT + x) * GROW + y];
+            vs[s] = tv(0, p0) * gv(0, p1, p2) + tv(1, p1) * gv(1, p0, p2) + tv(2, p2) * gv(2, p0, p1);
           }
           const float se = ws[0] + ws[3] + ws[4];
           const float so = ws[1] + ws[2] + ws[5];
@@ -739,11 +750,9 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
             const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
             sumf = fmaf(ws[s] + vs[s], br, sumf);
           }
-          // D = e_i + e_j + e_k - e_a - e_b - e_c formed in FP64 (no cancellation
-          // loss), its correctly rounded FP32 reciprocal
-          const double D = dab - __ldg(J.eps + o + gc);
+          const float D = dab - __ldg(J.epsf + o + gc);
           const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
-          rowsum = fmaf(sumf * mult, __frcp_rn((float)D), rowsum);
+          rowsum = fmaf(sumf * mult, __frcp_rn(D), rowsum);
         }
         acc += (double)rowsum;
       }
@@ -873,22 +882,20 @@ __global__ void to_f32(const double *__restrict__ in, long long n, float *__rest
 
 struct WtShape {
   int stages, nprod;
-  size_t slot, sum_off, smem;
+  size_t slot, smem;
 };
 
 // Shared-memory plan of a W-term launch whose widest N chunk is ncmax.
 WtShape wt_shape(int S, int ncmax) {
   WtShape s{};
   s.slot = (size_t)S * A_BLK + (size_t)S * ncmax * 32;
-  const size_t sum_bytes = (size_t)MROWS * (ncmax + 4) * 4;
-  const long long st = ((long long)SMEM_DYN_MAX - 1024 - (long long)sum_bytes) / (long long)s.slot;
+  const long long st = ((long long)SMEM_DYN_MAX - 1024) / (long long)s.slot;
   s.stages = (int)std::min<long long>(MAX_STAGES, st);
   // The producers' parity waits on the empty barriers stay unambiguous only
   // while a producer is at most one ring cycle ahead of a stage's last use,
   // which the in-order MMA consumer guarantees when stages >= producers.
   s.nprod = std::min(NPROD, s.stages);
-  s.sum_off = (size_t)s.stages * s.slot;
-  s.smem = 1024 + s.sum_off + sum_bytes;
+  s.smem = 1024 + (size_t)s.stages * s.slot;
   return s;
 }
 
@@ -922,7 +929,6 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
   wb.stages = sh.stages;
   wb.nprod = sh.nprod;
   wb.slot = sh.slot;
-  wb.sum_off = sh.sum_off;
   *wsmem = sh.smem;
   long long etotal = 0;
   for (int j = 0; j < eb.njobs; ++j) {
@@ -957,7 +963,6 @@ SplitGeom split_geom(int o, int v, int S) {
   const int vp = g.kbv * KB;
   g.nch = (vp + NCMAX - 1) / NCMAX;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
-  g.ys = g.nc + 4;
   g.vc = (v + 3) / 4 * 4;
   // Triplets per block: about 16 W-term items per SM of a 152-SM GPU, at most
   // 64 and at most the number of triplets.
@@ -984,6 +989,7 @@ SplitLayout split_layout(int o, int v, int S) {
   L.tb = take(b_v);
   L.hb = take(b_o);
   L.t1f = take((size_t)o * v * 4);
+  L.epsf = take((size_t)(o + v) * 4);
   L.ovovf = take((size_t)o * v * o * v * 4);
   L.y = take((size_t)g.nb * 3 * v * v * g.vc * 4);
   L.total = off;
@@ -1001,11 +1007,12 @@ cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, 
   build_image<<<blocks, thr, 0, st>>>(4, in.t2, g, b + L.tb);
   build_image<<<blocks, thr, 0, st>>>(5, in.ovoo, g, b + L.hb);
   to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)g.o * g.v, (float *)(b + L.t1f));
+  to_f32<<<blocks, thr, 0, st>>>(in.eps, (long long)(g.o + g.v), (float *)(b + L.epsf));
   to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)g.o * g.v * g.o * g.v, (float *)(b + L.ovovf));
   return cudaGetLastError();
 }
 
-int split_prep_launches() { return 8; }
+int split_prep_launches() { return 9; }
 
 WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt) {
   const unsigned char *b = (const unsigned char *)ws;
@@ -1052,6 +1059,7 @@ cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *
   J.orb = w.orb;
   J.eps = in.eps;
   J.t1f = (const float *)(b + L.t1f);
+  J.epsf = (const float *)(b + L.epsf);
   J.ovovf = (const float *)(b + L.ovovf);
   J.y = (const float *)(b + L.y);
   J.partial = w.partial;
