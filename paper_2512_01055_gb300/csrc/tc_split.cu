@@ -81,7 +81,8 @@ constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
 
 // energy kernel
-constexpr int EN_THREADS = 512;
+constexpr int EN_CONSUMERS = 512;        // repack + compute threads
+constexpr int EN_THREADS = EN_CONSUMERS + 32;   // plus one warp that issues the TMA loads
 constexpr int EN_SLOTS = 2;               // staging slots of three 16^3 boxes
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
 constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
@@ -578,6 +579,8 @@ __device__ __forceinline__ void ecur_issue(const EnBatch &B, const ECur &c, floa
   for (int g = 0; g < 3; ++g) tma_load_4d(dst + g * NT * NT * NT, &J.ymap, Z, Y, X, f0 + g, bar);
 }
 
+__device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EN_CONSUMERS) : "memory"); }
+
 __global__ void __launch_bounds__(EN_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ EnBatch B) {
   extern __shared__ __align__(1024) unsigned char en_raw[];
@@ -585,14 +588,14 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
   float *stg = Wsm + 6 * WBLK;                                              // slots x 3 boxes
   float *gsm = stg + EN_SLOTS * 3 * NT * NT * NT;                           // G tiles [3][6][16][17]
   float *t1s = gsm + GV_FLOATS;                                             // t1 [3 occ][3 tiles][16]
-  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS];
-  __shared__ double red[EN_THREADS / 32];
-  __shared__ int en_ok;
+  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS];
+  __shared__ double red[EN_CONSUMERS / 32];
+  __shared__ volatile int en_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int BOXF = NT * NT * NT;
 
   if (tid == 0) {
-    for (int k = 0; k < EN_SLOTS; ++k) mbar_init(&full_bar[k], 1);
+    for (int k = 0; k < EN_SLOTS; ++k) { mbar_init(&full_bar[k], 1); mbar_init(&empty_bar[k], 1); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     en_ok = 1;
   }
@@ -602,14 +605,41 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
   cc.gi = blockIdx.x;
   cc.jc = 0;
   ecur_item(B, cc);
-  ECur pc = cc;                                      // producer cursor (used by thread 0)
-  long long issued = 0;
-  if (tid == 0) {
-    for (int k = 0; k < EN_SLOTS && pc.valid; ++k) {
-      ecur_issue(B, pc, stg + (size_t)k * 3 * BOXF, &full_bar[k]);
-      ++issued;
-      ecur_next(B, pc);
+  if (warp == EN_CONSUMERS / 32) {
+    // ------------------------------------------------ the producer warp: block
+    // loads in the consumers' order, each into the next free staging slot
+    if (lane == 0) {
+      ECur pc = cc;
+      long long k = 0;
+      bool ok = true;
+      while (ok && pc.valid) {
+        const int slot = (int)(k % EN_SLOTS);
+        const uint32_t a = smem_u32(&empty_bar[slot]);
+        const uint32_t par = (uint32_t)(((k / EN_SLOTS) & 1) ^ 1);
+        for (long long it = 0; !mbar_try(a, par); ++it) {
+          if (it == WAIT_LIMIT || ((it & 255) == 255 && !en_ok)) {
+            if (it == WAIT_LIMIT) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_EMPTY); }
+            ok = false;
+            break;
+          }
+          if ((it & 255) == 255) __nanosleep(64);
+        }
+        if (!ok) break;
+        ecur_issue(B, pc, stg + (size_t)slot * 3 * BOXF, &full_bar[slot]);
+        ++k;
+        ecur_next(B, pc);
+      }
+      // the last loads land before the CTA may exit (bounded; only the latest
+      // load into each slot can still be in flight)
+      for (long long kk = (k > EN_SLOTS ? k - EN_SLOTS : 0); kk < k; ++kk) {
+        const uint32_t a = smem_u32(&full_bar[kk % EN_SLOTS]);
+        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((kk / EN_SLOTS) & 1)); ++it)
+          if ((it & 255) == 255) __nanosleep(128);
+      }
     }
+    __syncwarp();
+    __syncthreads();
+    return;
   }
   double acc = 0.0;
   long long seq = 0;
@@ -622,13 +652,13 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     const int4 tr = J.trip[J.t0 + cc.tl];
     const int occ[3] = {tr.x, tr.y, tr.z};
     // an orbit's first block: load its V inputs (stored below, read by the compute)
-    constexpr int GV_PER = (GV_LOADS + EN_THREADS - 1) / EN_THREADS;
+    constexpr int GV_PER = (GV_LOADS + EN_CONSUMERS - 1) / EN_CONSUMERS;
     float gv[GV_PER];
     const bool first_block = cc.s == 0;
     if (first_block) {
 #pragma unroll
       for (int q = 0; q < GV_PER; ++q) {
-        const int idx = tid + EN_THREADS * q;
+        const int idx = tid + EN_CONSUMERS * q;
         float val = 0.f;
         if (idx < 3 * 6 * NT * NT) {
           const int op = idx / (6 * NT * NT), tp = (idx / (NT * NT)) % 6, u = (idx >> 4) & 15, w = idx & 15;
@@ -661,8 +691,8 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
       const float4 *sb = (const float4 *)(stg + (size_t)slot * 3 * BOXF);
       float *Wb = Wsm + cc.s * WBLK;
 #pragma unroll
-      for (int k = 0; k < BOXF / 4 / EN_THREADS; ++k) {
-        const int e4 = tid + k * EN_THREADS;              // float4 index: (x, y, z4)
+      for (int k = 0; k < BOXF / 4 / EN_CONSUMERS; ++k) {
+        const int e4 = tid + k * EN_CONSUMERS;            // float4 index: (x, y, z4)
         const float4 a0 = sb[e4], a1 = sb[BOXF / 4 + e4], a2 = sb[2 * BOXF / 4 + e4];
         const int x = e4 >> 6, y = (e4 >> 2) & 15, z = (e4 & 3) * 4;
         float *w = Wb + x * WX + y * WY + z;
@@ -674,20 +704,15 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
       if (first_block) {
 #pragma unroll
         for (int q = 0; q < GV_PER; ++q) {
-          const int idx = tid + EN_THREADS * q;
+          const int idx = tid + EN_CONSUMERS * q;
           if (idx < 3 * 6 * NT * NT) gsm[(idx >> 4) * GROW + (idx & 15)] = gv[q];
           else if (idx < GV_LOADS) t1s[idx - 3 * 6 * NT * NT] = gv[q];
         }
       }
     }
-    __syncthreads();
+    cons_bar();
     if (!en_ok) break;
-    // the slot is free: the producer refills it with the load two ahead
-    if (tid == 0 && pc.valid) {
-      ecur_issue(B, pc, stg + (size_t)slot * 3 * BOXF, &full_bar[slot]);
-      ++issued;
-      ecur_next(B, pc);
-    }
+    if (tid == 0) mbar_arrive(&empty_bar[slot]);       // the slot is free for the producer
     const bool orbit_done = ecur_last_of_orbit(cc);
     if (orbit_done) {
       // energy over the canonical points a >= b >= c of the orbit; threads
@@ -756,7 +781,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         }
         acc += (double)rowsum;
       }
-      __syncthreads();                       // W is rebuilt by the next orbit
+      cons_bar();                            // W is rebuilt by the next orbit
     }
     // next block load; an item ends when the cursor leaves it
     const long long gi_now = cc.gi;
@@ -770,23 +795,15 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
       if (lane == 0) red[warp] = acc;
-      __syncthreads();
+      cons_bar();
       if (tid == 0) {
         double tot = 0.0;
 #pragma unroll
-        for (int wq = 0; wq < EN_THREADS / 32; ++wq) tot += red[wq];
+        for (int wq = 0; wq < EN_CONSUMERS / 32; ++wq) tot += red[wq];
         partial[slot_now] = tot;
       }
-      __syncthreads();
+      cons_bar();
       acc = 0.0;
-    }
-  }
-  // after an abort: the loads still in flight land before the CTA exits (bounded)
-  if (tid == 0) {
-    for (long long k = seq; k < issued; ++k) {
-      const uint32_t a = smem_u32(&full_bar[k % EN_SLOTS]);
-      for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k / EN_SLOTS) & 1)); ++it)
-        if ((it & 255) == 255) __nanosleep(128);
     }
   }
   __syncthreads();
