@@ -95,6 +95,8 @@ typedef struct {
   int reserved;
   double wterm_seconds;      /* device time of the kernels that form W: FP64, the fused kernel (= kernel_seconds);
                                 split path, the W-term GEMM launches alone (blocking entry points only) */
+  double e_t5;               /* E[5]_ST: the part of E_(T) from the V factor of Eq. 1, sum (V r3(W))/D with the
+                                same weights; E[4] = e_t - e_t5 is the W r3(W)/D part (r3 is the bracket of Eq. 1) */
 } tc_result;
 
 /* Create a context on opt->device (opt may be NULL: device 0, defaults).

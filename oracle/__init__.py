@@ -42,7 +42,7 @@ import math
 
 import numpy as np
 
-__all__ = ["x_bracket_ijk", "w_ijk_all", "v_ijk_all", "d_ijk_all", "energy_eq1",
+__all__ = ["x_bracket_ijk", "w_ijk_all", "v_ijk_all", "d_ijk_all", "energy_eq1", "energy_parts_eq1",
            "w_abc_all", "triplet_energy", "energy_by_triplets", "triplet_weight"]
 
 
@@ -99,6 +99,34 @@ def abc_contribution(job, a: int, b: int, c: int) -> float:
                - 2.0 * np.einsum("jik->ijk", W) - 2.0 * np.einsum("ikj->ijk", W)
                - 2.0 * np.einsum("kji->ijk", W))
     return float(np.sum((W + V) * bracket / D))
+
+
+def abc_contribution_parts(job, a: int, b: int, c: int) -> tuple:
+    """The two parts of abc_contribution: (sum_ijk W r3(W)/D, sum_ijk V r3(W)/D),
+    r3(W) = 4W_ijk + W_jki + W_kij - 2W_jik - 2W_ikj - 2W_kji (the bracket of Eq. 1)."""
+    W = w_ijk_all(job, a, b, c)
+    V = v_ijk_all(job, a, b, c)
+    D = d_ijk_all(job, a, b, c)
+    bracket = (4.0 * W + np.einsum("jki->ijk", W) + np.einsum("kij->ijk", W)
+               - 2.0 * np.einsum("jik->ijk", W) - 2.0 * np.einsum("ikj->ijk", W)
+               - 2.0 * np.einsum("kji->ijk", W))
+    return float(np.sum(W * bracket / D)), float(np.sum(V * bracket / D))
+
+
+def energy_parts_eq1(job) -> tuple:
+    """(E[4], E[5]_ST): Eq. 1 with its factor (W + V) split into the W part and
+    the V part, same a >= b >= c weights; E_(T) = E[4] + E[5]_ST."""
+    t4, t5 = [], []
+    for a in range(job.v):
+        for b in range(a + 1):
+            for c in range(b + 1):
+                wgt = 2 - (a == b) - (b == c)
+                if wgt == 0:
+                    continue
+                e4, e5 = abc_contribution_parts(job, a, b, c)
+                t4.append(wgt * e4)
+                t5.append(wgt * e5)
+    return math.fsum(t4), math.fsum(t5)
 
 
 def energy_eq1(job) -> float:

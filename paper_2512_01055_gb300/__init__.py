@@ -55,7 +55,8 @@ class tc_result(ctypes.Structure):
                 ("prec", ctypes.c_int), ("slices", ctypes.c_int), ("o", ctypes.c_int), ("v", ctypes.c_int),
                 ("queue_seconds", ctypes.c_double), ("kernel_seconds", ctypes.c_double),
                 ("prep_seconds", ctypes.c_double), ("n_items", ctypes.c_longlong),
-                ("launches", ctypes.c_int), ("reserved", ctypes.c_int), ("wterm_seconds", ctypes.c_double)]
+                ("launches", ctypes.c_int), ("reserved", ctypes.c_int), ("wterm_seconds", ctypes.c_double),
+                ("e_t5", ctypes.c_double)]
 
 
 class TcError(RuntimeError):

@@ -141,15 +141,16 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
     rb.job[0] = tc::RedJob{d.n_trip, d.items_per_trip, o, w.trip, w.partial, e_trip, e_ijk_dev, dout};
     TC_CUDA(ctx, tc::launch_reduce(rb, st));
   }
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out, dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out + 2, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out, dout, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->host_out + 3, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TC_CUDA(ctx, cudaStreamSynchronize(st));
   int errflag = 0;
-  std::memcpy(&errflag, ctx->host_out + 2, sizeof(int));
+  std::memcpy(&errflag, ctx->host_out + 3, sizeof(int));
   if (errflag != 0)
     return fail(ctx, (errflag >= 11 && errflag <= 15) ? TC_ETIMEOUT : TC_EINTERNAL,
                 "device-side wait gave up (code %d)", errflag);
   out->e_t = ctx->host_out[0];
+  out->e_t5 = ctx->host_out[2];
   if (e_sub) {
     e_sub->assign((size_t)d.n_trip, 0.0);
     if (d.n_trip > 0) {

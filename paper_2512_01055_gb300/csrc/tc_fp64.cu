@@ -47,7 +47,7 @@ tc_fp64_kernel(const __grid_constant__ FpBatch B) {
   double *As = Ws + 6 * NT3;             // [6][NT2][LDA] particle A rows, one set per u
   double *Bs = As + 6 * NT2 * LDA;       // [6][NT][LDA]  particle B rows (t2 panels)
   __shared__ long long s_item;
-  __shared__ double s_red[THREADS / 32];
+  __shared__ double s_red[THREADS / 32], s_red5[THREADS / 32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -67,7 +67,7 @@ tc_fp64_kernel(const __grid_constant__ FpBatch B) {
     const int chunk = (int)(item % d.items_per_trip);
     const int4 tr = w.trip[t];
     const int occ[3] = {tr.x, tr.y, tr.z};
-    double acc = 0.0;
+    double acc = 0.0, acc5 = 0.0;                // E_(T) and its V part E[5]_ST
 
     const int ob0 = chunk * d.orb_per_item;
     const int ob1 = min(d.n_orb, ob0 + d.orb_per_item);
@@ -183,28 +183,35 @@ tc_fp64_kernel(const __grid_constant__ FpBatch B) {
         }
         const double se = ws[0] + ws[3] + ws[4];
         const double so = ws[1] + ws[2] + ws[5];
-        double sum = 0.0;
+        double sum = 0.0, sum5 = 0.0;
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
           const double br = 3.0 * ws[s] + (perm3_even(s) ? se - 2.0 * so : so - 2.0 * se);
           sum = fma(ws[s] + vs[s], br, sum);
+          sum5 = fma(vs[s], br, sum5);
         }
         const double D = eijk - (__ldg(in.eps + o + g[0]) + __ldg(in.eps + o + g[1]) + __ldg(in.eps + o + g[2]));
         const double mult = (g[0] == g[2]) ? 6.0 : ((g[0] == g[1] || g[1] == g[2]) ? 2.0 : 1.0);
-        acc += sum / (D * mult);
+        const double rdm = 1.0 / (D * mult);
+        acc = fma(sum, rdm, acc);
+        acc5 = fma(sum5, rdm, acc5);
       }
       __syncthreads();
     }
 
     // block reduction of the item's partial (fixed order -> deterministic)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (lane == 0) s_red[warp] = acc;
+    for (int off = 16; off > 0; off >>= 1) {
+      acc += __shfl_down_sync(0xffffffffu, acc, off);
+      acc5 += __shfl_down_sync(0xffffffffu, acc5, off);
+    }
+    if (lane == 0) { s_red[warp] = acc; s_red5[warp] = acc5; }
     __syncthreads();
     if (tid == 0) {
-      double s = 0.0;
-      for (int i2 = 0; i2 < THREADS / 32; ++i2) s += s_red[i2];
-      w.partial[item] = s;
+      double s = 0.0, s5 = 0.0;
+      for (int i2 = 0; i2 < THREADS / 32; ++i2) { s += s_red[i2]; s5 += s_red5[i2]; }
+      w.partial[2 * item] = s;
+      w.partial[2 * item + 1] = s5;
     }
     __syncthreads();
   }

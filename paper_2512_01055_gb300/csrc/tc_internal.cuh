@@ -43,7 +43,7 @@ struct Inputs {        // device pointers, layouts as in include/tc.h
 struct Work {
   const int4 *trip;    // (i, j, k, weight)
   const int4 *orb;     // (P, Q, R, 0) tile indices
-  double *partial;     // [n_items]
+  double *partial;     // [n_items][2]: the item's E_(T) part and its E[5]_ST (V r3(W)/D) part
   unsigned int *counter;
   int *err;            // device error flag (0 = fine)
 };
@@ -123,7 +123,7 @@ struct EnJob {           // one job's block of triplets in an energy launch
   const int4 *trip, *orb;
   const double *eps;
   const float *t1f, *epsf, *ovovf, *y;
-  double *partial;       // [n_items], slot t * items_per_trip + chunk
+  double *partial;       // [n_items][2], slot t * items_per_trip + chunk
   int t0, nt;
   long long item0;
 };
@@ -158,7 +158,7 @@ struct RedJob {
   const double *partial;
   double *e_trip;        // [n_trip] weighted triplet contributions
   double *e_ijk;         // optional [o][o][o]
-  double *out;           // [2]: E and sum |e|
+  double *out;           // [3]: E, sum |e| and E[5]_ST
 };
 struct RedBatch {
   int njobs;

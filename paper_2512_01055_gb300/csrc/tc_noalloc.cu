@@ -55,7 +55,7 @@ Carve carve(const tc::Dims &d) {
   size_t off = 0;
   c.trip = off;    off = al256(off + sizeof(int4) * (size_t)(d.n_trip > 0 ? d.n_trip : 1));
   c.orb = off;     off = al256(off + sizeof(int4) * (size_t)d.n_orb);
-  c.partial = off; off = al256(off + sizeof(double) * (size_t)(d.n_items > 0 ? d.n_items : 1));
+  c.partial = off; off = al256(off + 2 * sizeof(double) * (size_t)(d.n_items > 0 ? d.n_items : 1));
   c.e_trip = off;  off = al256(off + sizeof(double) * (size_t)(d.n_trip > 0 ? d.n_trip : 1));
   c.out = off;     off = al256(off + 4 * sizeof(double));
   c.counter = off; off = al256(off + 2 * sizeof(unsigned));

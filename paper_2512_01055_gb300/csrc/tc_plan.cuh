@@ -39,7 +39,7 @@ inline Layout make_layout(const Dims &d) {
   size_t off = 0;
   L.trip = off;    off = align256(off + sizeof(int4) * (size_t)std::max(1, d.n_trip));
   L.orb = off;     off = align256(off + sizeof(int4) * (size_t)std::max(1, d.n_orb));
-  L.partial = off; off = align256(off + sizeof(double) * (size_t)std::max<long long>(1, d.n_items));
+  L.partial = off; off = align256(off + 2 * sizeof(double) * (size_t)std::max<long long>(1, d.n_items));
   L.e_trip = off;  off = align256(off + sizeof(double) * (size_t)std::max(1, d.n_trip));
   L.out = off;     off = align256(off + 4 * sizeof(double));
   L.counter = off; off = align256(off + 2 * sizeof(unsigned));

@@ -88,8 +88,8 @@ struct Server {
   std::vector<cudaStream_t> prep_streams;
   unsigned *d_counter = nullptr;          // FP64 work counter (zeroed by the graph)
   int *d_err = nullptr;                   // split kernels' wait-limit flag
-  double *h_out = nullptr;                // pinned: 2 doubles per job of a reduction + err
-  double *d_out = nullptr;                // device: 2 doubles per job of a reduction
+  double *h_out = nullptr;                // pinned: 4 doubles per job of a reduction + err
+  double *d_out = nullptr;                // device: 4 doubles per job of a reduction (E, sum |e|, E[5]_ST)
   cudaGraph_t graph[N_GROUPS] = {};
   cudaGraphExec_t exec[N_GROUPS] = {};
   cudaGraphNode_t knode[N_GROUPS] = {};
@@ -122,8 +122,8 @@ tc_status Server::setup() {
   for (auto &s : prep_streams)
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return TC_ECUDA;
   if (cudaMalloc(&d_counter, 256) != cudaSuccess || cudaMalloc(&d_err, 256) != cudaSuccess ||
-      cudaMalloc(&d_out, sizeof(double) * 2 * MAX_BATCH) != cudaSuccess ||
-      cudaMallocHost(&h_out, sizeof(double) * (2 * MAX_BATCH + 1)) != cudaSuccess)
+      cudaMalloc(&d_out, sizeof(double) * 4 * MAX_BATCH) != cudaSuccess ||
+      cudaMallocHost(&h_out, sizeof(double) * (4 * MAX_BATCH + 1)) != cudaSuccess)
     return TC_ECUDA;
   cudaMemset(d_err, 0, 256);
   // keep freed job memory in the pool for reuse instead of returning it to the driver
@@ -355,10 +355,10 @@ void Server::finish(std::vector<std::shared_ptr<Req>> &done) {
       Req &q = *done[b0 + j];
       char *base = q.mem + q.off_ws;
       rb.job[j] = RedJob{q.d.n_trip, q.d.items_per_trip, q.o, q.w.trip, q.w.partial,
-                         (double *)(base + q.L.e_trip), nullptr, d_out + 2 * j};
+                         (double *)(base + q.L.e_trip), nullptr, d_out + 4 * j};
     }
     cudaError_t e = launch_reduce(rb, compute);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, compute);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, compute);
     for (int j = 0; j < n; ++j) cudaFreeAsync(done[b0 + j]->mem, compute);
     if (e == cudaSuccess) e = cudaStreamSynchronize(compute);
     std::lock_guard<std::mutex> lk(mu);
@@ -369,7 +369,8 @@ void Server::finish(std::vector<std::shared_ptr<Req>> &done) {
       active.erase(std::find(active.begin(), active.end(), r));
       if (e != cudaSuccess) { fail_job(r, TC_ECUDA); continue; }
       r->t_done = Clock::now();
-      r->res.e_t = h_out[2 * j];
+      r->res.e_t = h_out[4 * j];
+      r->res.e_t5 = h_out[4 * j + 2];
       r->state = St::Done;
       r->status = TC_OK;
       ++stats.completed;

@@ -589,7 +589,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
   float *gsm = stg + EN_SLOTS * 3 * NT * NT * NT;                           // G tiles [3][6][16][17]
   float *t1s = gsm + GV_FLOATS;                                             // t1 [3 occ][3 tiles][16]
   __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS];
-  __shared__ double red[EN_CONSUMERS / 32];
+  __shared__ double red[EN_CONSUMERS / 32], red5[EN_CONSUMERS / 32];
   __shared__ volatile int en_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int BOXF = NT * NT * NT;
@@ -641,7 +641,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     __syncthreads();
     return;
   }
-  double acc = 0.0;
+  double acc4 = 0.0, acc5 = 0.0;                     // the W and V parts of E_(T): E[4], E[5]_ST
   long long seq = 0;
   while (cc.valid) {
     const EnJob &J = B.job[cc.jc];
@@ -737,7 +737,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
           gab[op] = gsm[((op * 6 + tpair(0, 1)) * NT + la) * GROW + lb];
           gba[op] = gsm[((op * 6 + tpair(1, 0)) * NT + lb) * GROW + la];
         }
-        float rowsum = 0.f;                  // up to 8 points, added into acc in FP64 once
+        float rowsum4 = 0.f, rowsum5 = 0.f;  // up to 8 points, added into acc4 / acc5 in FP64 once
         for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
           const int gc = cc.tl3[2] * NT + lcc;
           if (gc >= v || gb < gc) continue;
@@ -769,17 +769,21 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
           }
           const float se = ws[0] + ws[3] + ws[4];
           const float so = ws[1] + ws[2] + ws[5];
-          float sumf = 0.f;
+          float sumf4 = 0.f, sumf5 = 0.f;
 #pragma unroll
           for (int s = 0; s < 6; ++s) {
             const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
-            sumf = fmaf(ws[s] + vs[s], br, sumf);
+            sumf4 = fmaf(ws[s], br, sumf4);
+            sumf5 = fmaf(vs[s], br, sumf5);
           }
           const float D = dab - __ldg(J.epsf + o + gc);
           const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
-          rowsum = fmaf(sumf * mult, __frcp_rn(D), rowsum);
+          const float rd = __frcp_rn(D);
+          rowsum4 = fmaf(sumf4 * mult, rd, rowsum4);
+          rowsum5 = fmaf(sumf5 * mult, rd, rowsum5);
         }
-        acc += (double)rowsum;
+        acc4 += (double)rowsum4;
+        acc5 += (double)rowsum5;
       }
       cons_bar();                            // W is rebuilt by the next orbit
     }
@@ -793,17 +797,22 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     if (!cc.valid || cc.gi != gi_now) {
       // the item's partial: fixed-order reduction over the block
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) red[warp] = acc;
+      for (int off = 16; off > 0; off >>= 1) {
+        acc4 += __shfl_down_sync(0xffffffffu, acc4, off);
+        acc5 += __shfl_down_sync(0xffffffffu, acc5, off);
+      }
+      if (lane == 0) { red[warp] = acc4; red5[warp] = acc5; }
       cons_bar();
       if (tid == 0) {
-        double tot = 0.0;
+        double tot4 = 0.0, tot5 = 0.0;
 #pragma unroll
-        for (int wq = 0; wq < EN_CONSUMERS / 32; ++wq) tot += red[wq];
-        partial[slot_now] = tot;
+        for (int wq = 0; wq < EN_CONSUMERS / 32; ++wq) { tot4 += red[wq]; tot5 += red5[wq]; }
+        partial[2 * slot_now] = tot4 + tot5;
+        partial[2 * slot_now + 1] = tot5;
       }
       cons_bar();
-      acc = 0.0;
+      acc4 = 0.0;
+      acc5 = 0.0;
     }
   }
   __syncthreads();

@@ -169,3 +169,27 @@ def test_planted_mistakes_are_caught():
     finally:
         oracle.abc_contribution = orig
     assert abs(oracle.energy_eq1(job) - e_so) <= 1e-12 * abs(e_so)
+
+
+# ---------------------------------------------------------------------------
+# E[4] and E[5]_ST: the W part and the V part of Eq. 1's factor (W + V).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("o,v,seed", [(3, 5, 21), (4, 6, 22)])
+def test_energy_parts_add_up(o, v, seed):
+    job = synth.make_job(o, v, seed)
+    e4, e5 = oracle.energy_parts_eq1(job)
+    e = oracle.energy_eq1(job)
+    assert abs((e4 + e5) - e) <= 1e-12 * (abs(e4) + abs(e5))
+
+
+def test_e5_structure_in_t1():
+    """V is linear in t1 and W does not depend on t1: E[5]_ST vanishes without t1
+    and is odd in t1, E[4] is the same for t1, -t1 and 0 (all exactly)."""
+    job = synth.make_job(4, 6, 23)
+    e4, e5 = oracle.energy_parts_eq1(job)
+    e4m, e5m = oracle.energy_parts_eq1(dataclasses.replace(job, t1=-job.t1))
+    e40, e50 = oracle.energy_parts_eq1(dataclasses.replace(job, t1=np.zeros_like(job.t1)))
+    assert e50 == 0.0
+    assert e5m == -e5 and e5 != 0.0
+    assert e4m == e4 == e40
