@@ -65,7 +65,8 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
                      std::vector<double> *e_sub = nullptr) {
   const bool split = (prec == TC_SPLIT_BF16);
   const int nt = split ? tc::split_tile() : tc::fp64_tile();
-  const tc::Dims d = tc::plan::make_dims(o, v, nt, subset ? (int)subset->size() : -1);
+  const tc::Dims d = tc::plan::make_dims(o, v, nt, subset ? (int)subset->size() : -1,
+                                         split ? tc::split_orb_per_item(o, v, slices) : 1);
   const tc::plan::Layout L = tc::plan::make_layout(d);
   const tc::SplitLayout SL = split ? tc::split_layout(o, v, slices) : tc::SplitLayout{};
   const size_t need = L.total + SL.total;
@@ -96,8 +97,8 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   if (d.n_items > 0) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     if (split) {
-      // blocks of nb triplets: W-term GEMMs into the W-term buffer, then the
-      // energy over the block's orbits
+      // blocks of nb triplets: the three W-term GEMM launches sum W into the
+      // W buffer, then the energy launch runs over the block's orbits
       const int nb = SL.g.nb;
       nblocks = (d.n_trip + nb - 1) / nb;
       while ((int)ctx->wev.size() < 2 * nblocks) {
@@ -119,7 +120,7 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
         TC_CUDA(ctx, tc::en_job(&eb.job[0], d, SL, ctx->ws_split.p, in, w, t0, nt));
         TC_CUDA(ctx, tc::launch_split_block(wb, eb, slices, ctx->num_sms, st, ctx->wev[2 * blk], ctx->wev[2 * blk + 1]));
       }
-      launches += 2 * nblocks - 1;
+      launches += (tc::SPLIT_WT_LAUNCHES + 1) * nblocks - 1;
     } else {
       int per_sm = 0;
       TC_CUDA(ctx, tc::fp64_blocks_per_sm(&per_sm));
@@ -211,7 +212,8 @@ size_t tc_workspace_bytes(int o, int v, int prec, int slices) {
   if (o <= 0 || v <= 0) return 0;
   const bool split = (prec == TC_SPLIT_BF16);
   if (split && slices <= 0) slices = 3;
-  const tc::Dims d = tc::plan::make_dims(o, v, split ? tc::split_tile() : tc::fp64_tile());
+  const tc::Dims d = split ? tc::plan::make_dims(o, v, tc::split_tile(), -1, tc::split_orb_per_item(o, v, slices))
+                           : tc::plan::make_dims(o, v, tc::fp64_tile());
   return tc::plan::make_layout(d).total + (split ? tc::split_layout(o, v, slices).total : 0);
 }
 

@@ -105,7 +105,8 @@ struct WtJob {           // one job's block of triplets in a W-term launch
   const int4 *trip;      // the job's triplet table
   int t0, nt;            // triplets [t0, t0 + nt) of the table
   const unsigned char *pa, *pa2, *hc, *hc2, *tb, *hb;
-  float *y;              // W-term buffer [nt][3][a][b][vc]: F(i,j,k)[ab,c], F(i,k,j)[ac,b], F(j,k,i)[bc,a] at c
+  float *y;              // W buffer [nt][a][b][vc]: W_abc = F(i,j,k)[ab,c] + F(i,k,j)[ac,b] + F(j,k,i)[bc,a]
+  int gsel;              // which F this launch forms: 0 F(i,j,k) (stores), 1 F(i,k,j), 2 F(j,k,i) (add)
   long long item0;       // first global item of this job in the launch (set by the launcher)
 };
 struct WtBatch {
@@ -117,12 +118,17 @@ struct WtBatch {
   WtJob job[MAX_BATCH];
 };
 struct EnJob {           // one job's block of triplets in an energy launch
-  CUtensorMap ymap;      // 4-D map of the W-term buffer: (c, b, a, 3 * triplet + F)
+  CUtensorMap ymap;      // 4-D map of the W buffer: (c, b, a, triplet)
+  CUtensorMap gmap;      // 5-D map of the FP32 (p u|q w) in both orders
+  CUtensorMap tmap;      // 2-D map of the FP32 t1
   Dims d;
   SplitGeom g;
   const int4 *trip, *orb;
   const double *eps;
-  const float *t1f, *epsf, *ovovf, *y;
+  const float *t1f;      // t1 [o][vc]
+  const float *epsf;     // eps as float pairs: [0, o+v) hi, [o+v, 2(o+v)) lo
+  const float *ovovf;    // [2][o][v][o][vc]: (p u|q w) at [0][p][u][q][w] and [1][q][w][p][u]
+  const float *y;
   double *partial;       // [n_items][2], slot t * items_per_trip + chunk
   int t0, nt;
   long long item0;
@@ -134,6 +140,9 @@ struct EnBatch {
   EnJob job[MAX_BATCH];
 };
 int split_tile();
+// Orbits per energy work item of the split path: about 8 items per SM of a
+// 152-SM GPU in each energy launch, so the per-item reduction is amortised.
+int split_orb_per_item(int o, int v, int S);
 SplitGeom split_geom(int o, int v, int S);
 SplitLayout split_layout(int o, int v, int S);
 cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st);
@@ -142,13 +151,17 @@ WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int
 // Energy job of triplets [t0, t0 + nt); encodes its tensor map (driver entry point).
 cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w,
                    int t0, int nt);
-// One block of triplets: the W-term launch, then the energy launch, on st.
-// w0 / w1 (optional) are recorded around the W-term launch.
+// W-term launches per block of triplets: one per F, in the order gsel = 0, 1, 2.
+constexpr int SPLIT_WT_LAUNCHES = 3;
+// One block of triplets: the three W-term launches, then the energy launch,
+// on st.  w0 / w1 (optional) are recorded around the W-term launches.
 cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cudaStream_t st,
                                cudaEvent_t w0 = nullptr, cudaEvent_t w1 = nullptr);
-// Prepare both batches as launch_split_block would and fill kernel-node
-// parameters of its two launches; wargs[0] / eargs[0] point to wb / eb.
-cudaError_t split_block_params(WtBatch &wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
+// Prepare the batches as launch_split_block would and fill the kernel-node
+// parameters of its launches: wb[0] is filled by the caller and copied into
+// wb[1], wb[2] (gsel 1, 2); wargs[f] / wp[f] belong to wb[f] (f < 3), eargs[0]
+// / ep to eb.  The nodes must run in the order wp[0], wp[1], wp[2], ep.
+cudaError_t split_block_params(WtBatch *wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
                                cudaKernelNodeParams *wp, cudaKernelNodeParams *ep);
 
 // ---------------------------------------------------------------- reduction

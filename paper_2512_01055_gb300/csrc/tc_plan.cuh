@@ -13,7 +13,8 @@ namespace plan {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // n_trip_override >= 0: the job processes that many listed triplets.
-inline Dims make_dims(int o, int v, int nt, int n_trip_override = -1) {
+// min_opi: fewest orbits per work item.
+inline Dims make_dims(int o, int v, int nt, int n_trip_override = -1, int min_opi = 1) {
   Dims d{};
   d.o = o;
   d.v = v;
@@ -24,7 +25,8 @@ inline Dims make_dims(int o, int v, int nt, int n_trip_override = -1) {
   d.n_orb = (int)(T * (T + 1) * (T + 2) / 6);
   const long long pairs = (long long)d.n_trip * d.n_orb;
   const long long target = 4LL << 20;   // at most ~4M partials
-  d.orb_per_item = (int)std::max<long long>(1, (pairs + target - 1) / target);
+  d.orb_per_item = (int)std::max<long long>(std::max(1, min_opi), (pairs + target - 1) / target);
+  d.orb_per_item = std::min(d.orb_per_item, std::max(1, d.n_orb));
   d.items_per_trip = (d.n_orb + d.orb_per_item - 1) / d.orb_per_item;
   d.n_items = (long long)d.n_trip * d.items_per_trip;
   return d;

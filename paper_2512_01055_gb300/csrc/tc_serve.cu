@@ -92,8 +92,8 @@ struct Server {
   double *d_out = nullptr;                // device: 4 doubles per job of a reduction (E, sum |e|, E[5]_ST)
   cudaGraph_t graph[N_GROUPS] = {};
   cudaGraphExec_t exec[N_GROUPS] = {};
-  cudaGraphNode_t knode[N_GROUPS] = {};
-  cudaGraphNode_t enode[N_GROUPS] = {};   // split groups: the energy launch after the W-term launch
+  cudaGraphNode_t knode[N_GROUPS][SPLIT_WT_LAUNCHES] = {};   // FP64 group: [0] only; split: the W-term chain
+  cudaGraphNode_t enode[N_GROUPS] = {};   // split groups: the energy launch after the W-term launches
   double rate[N_GROUPS] = {3e7, 4e8, 3e8, 2e8};   // cost units per second (refined as iterations run)
   int rr = 0;                             // round-robin cursor over groups
   int fault_alloc = 0, fault_stall_ms = 0;
@@ -264,10 +264,10 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     if (!q.waited) { cudaStreamWaitEvent(compute, q.ready, 0); q.waited = true; }
     if (!q.started) { q.started = true; q.t_start = Clock::now(); }
   }
-  void *args[1], *eargs[1];
-  cudaKernelNodeParams kp{}, ep{};
+  void *args[SPLIT_WT_LAUNCHES], *eargs[1];
+  cudaKernelNodeParams kp[SPLIT_WT_LAUNCHES] = {}, ep{};
   static thread_local FpBatch fb;
-  static thread_local WtBatch wb;
+  static thread_local WtBatch wb[SPLIT_WT_LAUNCHES];
   static thread_local EnBatch eb;
   long long total = 0;
   double cost = 0;
@@ -285,26 +285,27 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     }
     fb.total_items = total;
     const long long grid = std::min<long long>((long long)ctx->num_sms * fp64_per_sm, total);
-    fp64_node_params(fb, (int)grid, args, &kp);
+    fp64_node_params(fb, (int)grid, args, &kp[0]);
   } else {
-    wb = WtBatch{};
+    wb[0] = WtBatch{};
     eb = EnBatch{};
-    wb.njobs = eb.njobs = nj;
-    wb.err = eb.err = d_err;
+    wb[0].njobs = eb.njobs = nj;
+    wb[0].err = eb.err = d_err;
     for (int j = 0; j < nj; ++j) {
       Req &q = *jobs[j];
       const Inputs in{q.din[0], q.din[1], q.din[2], q.din[3], q.din[4], q.din[5]};
       const int t0 = (int)q.next_item, nt = (int)take[j];
-      wb.job[j] = wt_job(q.SL, q.mem + q.off_split, q.w.trip, t0, nt);
+      wb[0].job[j] = wt_job(q.SL, q.mem + q.off_split, q.w.trip, t0, nt);
       if (e == cudaSuccess) e = en_job(&eb.job[j], q.d, q.SL, q.mem + q.off_split, in, q.w, t0, nt);
       total += take[j];
       cost += take[j] * q.cost_per_item;
     }
-    if (e == cudaSuccess) e = split_block_params(wb, eb, g + 1, ctx->num_sms, args, eargs, &kp, &ep);
+    if (e == cudaSuccess) e = split_block_params(wb, eb, g + 1, ctx->num_sms, args, eargs, kp, &ep);
   }
   if (e != cudaSuccess) return false;
   if (!exec[g]) {
-    // the group's graph: [zero the work counter] -> [multi-job kernel]
+    // the group's graph: FP64, [zero the work counter] -> [multi-job kernel];
+    // split, [W-term F0] -> [F1] -> [F2] -> [energy]
     e = cudaGraphCreate(&graph[g], 0);
     cudaGraphNode_t mnode = nullptr;
     if (e == cudaSuccess && g == 0) {
@@ -316,12 +317,20 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
       mp.height = 1;
       e = cudaGraphAddMemsetNode(&mnode, graph[g], nullptr, 0, &mp);
     }
-    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&knode[g], graph[g], mnode ? &mnode : nullptr, mnode ? 1 : 0, &kp);
-    if (e == cudaSuccess && g != 0) e = cudaGraphAddKernelNode(&enode[g], graph[g], &knode[g], 1, &ep);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&knode[g][0], graph[g], mnode ? &mnode : nullptr, mnode ? 1 : 0, &kp[0]);
+    if (g != 0) {
+      for (int f = 1; f < SPLIT_WT_LAUNCHES && e == cudaSuccess; ++f)
+        e = cudaGraphAddKernelNode(&knode[g][f], graph[g], &knode[g][f - 1], 1, &kp[f]);
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(&enode[g], graph[g], &knode[g][SPLIT_WT_LAUNCHES - 1], 1, &ep);
+    }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec[g], graph[g], 0);
   } else {
-    e = cudaGraphExecKernelNodeSetParams(exec[g], knode[g], &kp);
-    if (e == cudaSuccess && g != 0) e = cudaGraphExecKernelNodeSetParams(exec[g], enode[g], &ep);
+    e = cudaGraphExecKernelNodeSetParams(exec[g], knode[g][0], &kp[0]);
+    if (g != 0) {
+      for (int f = 1; f < SPLIT_WT_LAUNCHES && e == cudaSuccess; ++f)
+        e = cudaGraphExecKernelNodeSetParams(exec[g], knode[g][f], &kp[f]);
+      if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(exec[g], enode[g], &ep);
+    }
   }
   const auto t0 = Clock::now();
   if (e == cudaSuccess) e = cudaGraphLaunch(exec[g], compute);
@@ -510,7 +519,8 @@ tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket) {
   r->group = tc::group_of(prec, slices);
   r->dev_inputs = (job->flags & TC_JOB_DEVICE_INPUTS) != 0;
   const bool split = prec == TC_SPLIT_BF16;
-  r->d = tc::plan::make_dims(o, v, split ? tc::split_tile() : tc::fp64_tile());
+  r->d = split ? tc::plan::make_dims(o, v, tc::split_tile(), -1, tc::split_orb_per_item(o, v, slices))
+              : tc::plan::make_dims(o, v, tc::fp64_tile());
   r->L = tc::plan::make_layout(r->d);
   if (split) r->SL = tc::split_layout(o, v, slices);
   r->footprint = (r->dev_inputs ? 0 : tc::plan::align256(tc::plan::input_bytes(o, v))) + r->L.total + r->SL.total;

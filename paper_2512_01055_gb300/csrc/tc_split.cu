@@ -21,22 +21,25 @@
 // pairs (x, y), N = v and K = 2v + 2o (four segments), so the tensor cores run
 // with N up to 224 instead of the 16-wide panels a tile-local W would allow.
 //
-// W-term kernel.  A work item is (128-row M tile, triplet, F, N chunk); items
-// run M-tile-major so the triplets of one launch share A tiles through L2.
+// W-term kernel.  One launch forms one F for a block of triplets; a work item
+// is (128-row M tile, triplet, N chunk), M-tile-major so the triplets of the
+// launch share A tiles through L2.
 // Per K block of 16 the MMA warp issues one MMA per slice pair: level 0 into
 // accumulator L0, levels >= 1 into L1 (TMEM columns [0, nc) and [nc, 2nc)).
 // The FP32 accumulation along K rounds systematically, so L0 is restarted
 // every KCHAIN blocks (256 K values): the drain warps (a thread holds one tile
 // row, half its columns) add each finished chain into the row's FP32 sum in
-// registers; on the last chain they add L1 and write the row into the job's
-// W-term buffer in [a][b][c] orientation, Y[triplet][F][a][b][c], so that the
-// three F contributions to one W element sit at the same place.  Shared memory
-// holds only the operand pipeline.
+// registers; on the last chain they add L1 and write the row, in [a][b][c]
+// orientation, into the job's W buffer Y[triplet][a][b][c].  The three F
+// launches of a block run in order: the first stores, the other two add their
+// rows to the stored values (L2 reductions), so Y ends as W with each
+// element's three contributions added in one fixed order.  Shared memory holds only the
+// operand pipeline.
 //
 // Energy kernel.  A work item is (triplet, chunk of tile orbits) as in the
-// FP64 path.  Per orbit it sums the three F buffers' 16^3 boxes of each of the
-// six W blocks (TMA loads) in shared memory and evaluates the Eq. 1 bracket at
-// the orbit's canonical points, writing one FP64 partial per item.
+// FP64 path.  Per orbit it loads the six 16^3 W blocks (TMA) into shared
+// memory and evaluates the Eq. 1 bracket at the orbit's canonical points,
+// writing FP64 partials (E_(T) and its V part) per item.
 //
 // Operand images.  The slicer writes every operand block of 16 K values
 // directly in the tensor core's K-major no-swizzle layout (8-row x 16-byte
@@ -81,20 +84,21 @@ constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
 
 // energy kernel
-constexpr int EN_CONSUMERS = 512;        // repack + compute threads
-constexpr int EN_THREADS = EN_CONSUMERS + 32;   // plus one warp that issues the TMA loads
-constexpr int EN_SLOTS = 2;               // staging slots of three 16^3 boxes
+constexpr int EN_CONSUMERS = 512;        // copy + compute threads
+constexpr int EN_WARPS = EN_CONSUMERS / 32;
+constexpr int EN_THREADS = EN_CONSUMERS + 32;   // plus one warp that walks the work and issues the TMA loads
+constexpr int BOXF = NT * NT * NT;        // floats of a 16^3 box
+constexpr int EN_SLOTS = 5;               // W staging slots (one box each)
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
 constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
-// V inputs of an orbit in shared memory: G_pq^uw = (p u|q w) for the three
-// occupied pairs (jk, ik, ij) and the six ordered pairs of the orbit's tile
-// positions (rows padded to 17), and t1 for the three occupied indices and
-// three tile positions
-constexpr int GROW = 17;
-constexpr int GV_FLOATS = 3 * 6 * NT * GROW;
-constexpr int T1_FLOATS = 3 * 3 * NT;
-constexpr int GV_LOADS = 3 * 6 * NT * NT + T1_FLOATS;
-constexpr int EN_SMEM = 1024 + 6 * WBLK * 4 + EN_SLOTS * 3 * 4096 * 4 + (GV_FLOATS + T1_FLOATS) * 4;
+// An orbit's V set: 18 G tiles of 16 x 16 and 9 t1 rows of 16 (each t1 row at
+// a 128-byte TMA destination)
+constexpr int G_FLOATS = 18 * NT * NT;
+constexpr int T1_ROW = 32;
+constexpr int GSET_FLOATS = G_FLOATS + 9 * T1_ROW;
+constexpr int GSET_TX = (G_FLOATS + 9 * NT) * 4;   // bytes the TMA delivers per set
+constexpr int EN_SMEM = 1024 + (EN_SLOTS * BOXF + 2 * GSET_FLOATS + 6 * WBLK) * 4;
+static_assert(EN_SMEM + 1024 <= 232448, "energy kernel shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -187,12 +191,12 @@ __host__ __device__ __forceinline__ void orbit_blocks(const int tl[3], int blk[6
 
 // ---------------------------------------------------------------- W-term kernel
 
-// Item q of a job -> (M tile, triplet in the block, F, N chunk), M-tile-major.
+// Item q of a job -> (M tile, triplet in the block, N chunk), M-tile-major; a
+// launch forms one F (J.gsel) for every triplet of the block.
 __device__ __forceinline__ void wt_decode(const WtJob &J, long long q, int &m, int &tl, int &g, int &nci) {
   nci = (int)(q % J.g.nch);
   q /= J.g.nch;
-  g = (int)(q % 3);
-  q /= 3;
+  g = J.gsel;
   tl = (int)(q % J.nt);
   m = (int)(q / J.nt);
 }
@@ -447,39 +451,41 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         if (et == 0) mbar_arrive(&accempty_bar);
         aphase ^= 1u;
         if (!last) continue;
-        // The last chain: store the row into the W-term buffer of its F in
-        // [a][b][c] orientation.  For F(i,k,j)[ac,b] and F(j,k,i)[bc,a] the warp's
-        // 32 lanes hold 32 consecutive c, so the stores column by column are
-        // 128-byte coalesced.
+        // The last chain: the row goes into the job's W buffer Y[triplet][a][b][c].
+        // F(i,j,k) stores its row (a, b) contiguously; F(i,k,j) (row (a, c)) and
+        // F(j,k,i) (row (b, c)) add theirs column by column with reductions in
+        // L2 (not read back, so nothing waits on them).  Each W element has one
+        // writer per launch and the launches are ordered, so every element is
+        // the same IEEE sum on every run.  The warp's 32 lanes hold 32
+        // consecutive c, so each column's reductions cover 128 contiguous bytes.
         int m, tl, g, nci;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
         const int vo = J.g.v, vc = J.g.vc;
         const int row = m * MROWS + lrow;
-        if (row < vo * vo) {
-          const int zb = nci * nc + g0 * 16;
-          float *Wf = J.y + (size_t)(tl * 3 + g) * vo * vo * vc;
-          if (g == 0) {                                  // row (a, b), columns c
-            float *dst = Wf + (size_t)row * vc + zb;
+        if (row >= vo * vo) continue;
+        const int zb = nci * nc + g0 * 16;              // first column this thread holds
+        float *Wf = J.y + (size_t)tl * vo * vo * vc;
+        if (g == 0) {
+          float *dst = Wf + (size_t)row * vc + zb;
 #pragma unroll
-            for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-              if (gi2 >= my) break;
+          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+            if (gi2 >= my) break;
 #pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (zb + gi2 * 16 + 4 * e < vo)
-                  *(float4 *)(dst + gi2 * 16 + 4 * e) =
-                      make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
-            }
-          } else {                                       // row (p, c); column b (g = 1) or a (g = 2)
-            const int p = row / vo, c = row - p * vo;
-            const size_t st = (g == 1) ? (size_t)vc : (size_t)vo * vc;
-            float *dst = Wf + ((g == 1) ? (size_t)p * vo * vc : (size_t)p * vc) + c + (size_t)zb * st;
+            for (int e = 0; e < 4; ++e)
+              if (zb + gi2 * 16 + 4 * e < vo)
+                *(float4 *)(dst + gi2 * 16 + 4 * e) =
+                    make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
+          }
+        } else {
+          const int p = row / vo, c = row - p * vo;
+          const size_t st = (g == 1) ? (size_t)vc : (size_t)vo * vc;
+          float *dst = Wf + ((g == 1) ? (size_t)p * vo * vc : (size_t)p * vc) + c + (size_t)zb * st;
 #pragma unroll
-            for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-              if (gi2 >= my) break;
+          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+            if (gi2 >= my) break;
 #pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (zb + gi2 * 16 + e < vo) dst[(size_t)(gi2 * 16 + e) * st] = v[gi2][e];
-            }
+            for (int e = 0; e < 16; ++e)
+              if (zb + gi2 * 16 + e < vo) atomicAdd(dst + (size_t)(gi2 * 16 + e) * st, v[gi2][e]);
           }
         }
       }
@@ -497,20 +503,40 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
 
 // ---------------------------------------------------------------- energy kernel
 //
-// One CTA per SM walks its items (triplet, orbit chunk); every distinct W block
-// of an orbit is one "block load": three 16^3 boxes, one from each F buffer,
-// fetched by TMA (4-D tensor map over the job's W-term buffer, zero-filled
-// where an index reaches v) into a staging slot.  Thread 0 keeps a second
-// cursor two block loads ahead and issues them as slots free up, so the loads
-// of the next blocks (and of the next orbit) fly while the current block is
-// repacked and the orbit's energy is evaluated.
+// One CTA per SM walks its items (triplet, chunk of consecutive orbits).  The
+// producer warp owns the walk: per orbit it fills one of two "V sets" (the
+// eighteen 16 x 16 G tiles and nine 16-entry t1 rows the orbit's V needs, by
+// TMA, plus a small record of the orbit: triplet, tiles, distinct blocks,
+// item) and then loads the orbit's distinct W blocks (one 16^3 box of the
+// triplet's W buffer each, 4-D tensor map, zero-filled where an index reaches
+// v) into a ring of staging slots.  The consumer warps copy each box into its
+// padded W block, release the slot warp by warp, evaluate the orbit's energy
+// once its blocks are in place and release the V set; so the next orbit's
+// loads fly while the current orbit's energy is evaluated, and the consumers
+// meet at a CTA barrier only twice per orbit.
+//
+// G tiles: G_pq^uw = (p u|q w) for the occupied pairs (p, q) = (j, k), (i, k),
+// (i, j) and the six ordered pairs (u, w) of the orbit's tile positions.  The
+// FP32 copy of ovov holds (p u|q w) in both orders, [p][u][q][w] and
+// [q][w][p][u], so each tile lands in the orientation whose reads in the
+// energy loop are free of bank conflicts: [u][w] for (a,b), (a,c), (c,a),
+// (c,b) and [w][u] for (b,a), (b,c).
 
 // Index of the ordered pair (u, w) of distinct tile positions:
 // (0,1) (1,0) (0,2) (2,0) (1,2) (2,1)
 __host__ __device__ constexpr int tpair(int u, int w) {
   return (u == 0) ? (w == 1 ? 0 : 2) : (u == 1) ? (w == 0 ? 1 : 4) : (w == 0 ? 3 : 5);
 }
+__host__ __device__ constexpr int tpair_u(int tp) { return tp == 0 || tp == 2 ? 0 : (tp == 1 || tp == 4 ? 1 : 2); }
+__host__ __device__ constexpr int tpair_w(int tp) { return tp == 1 || tp == 3 ? 0 : (tp == 0 || tp == 5 ? 1 : 2); }
+__host__ __device__ constexpr bool tpair_swapped(int tp) { return tp == 1 || tp == 4; }
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3}], [%4];"
+               :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+               : "memory");
+}
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint64_t *bar) {
   asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -518,65 +544,35 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
                :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
                : "memory");
 }
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+  asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+               " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+               :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+               : "memory");
+}
 
-// Position in the sequence of block loads of a CTA.
-struct ECur {
-  long long gi;        // global item
-  int jc;              // its job
-  int tl, ob, ob1;     // triplet in the block; current orbit; end of the item's orbits
-  int s;               // distinct block (formal permutation index) of the orbit
-  int tl3[3], blk[6];
-  bool valid;
+// What the consumers need to know about the orbit of a V set.
+struct OrbMeta {
+  long long pidx;      // partial slot of the orbit's item
+  float eh, el;        // e_i + e_j + e_k as a float pair (hi + lo)
+  int jc, tl;          // job and triplet in the job's block
+  int tl3[3];          // tiles P >= Q >= R
+  int blk[6];          // distinct block of each formal permutation (orbit_blocks)
+  int last;            // last orbit of its item
+  int valid;           // 0: no more orbits
 };
 
-__device__ __forceinline__ void ecur_orbit(ECur &c) {
-  orbit_blocks(c.tl3, c.blk);
-  c.s = 0;                                           // the identity block is always distinct
+// Float pair arithmetic (Knuth's TwoSum): h + l carries about 48 bits.
+__device__ __forceinline__ void ff_add(float &h, float &l, float x) {
+  const float s = h + x, bp = s - h;
+  l += (h - (s - bp)) + (x - bp);
+  h = s;
 }
-__device__ __forceinline__ void ecur_item(const EnBatch &B, ECur &c) {
-  c.valid = c.gi < B.total_items;
-  if (!c.valid) return;
-  while (c.jc + 1 < B.njobs && c.gi >= B.job[c.jc + 1].item0) ++c.jc;
-  const EnJob &J = B.job[c.jc];
-  const long long q = c.gi - J.item0;
-  c.tl = (int)(q / J.d.items_per_trip);
-  const int chunk = (int)(q % J.d.items_per_trip);
-  c.ob = chunk * J.d.orb_per_item;
-  c.ob1 = min(J.d.n_orb, c.ob + J.d.orb_per_item);
-  const int4 og = J.orb[c.ob];                       // the item's first orbit; the next ones follow
-  c.tl3[0] = og.x; c.tl3[1] = og.y; c.tl3[2] = og.z;
-  ecur_orbit(c);
-}
-__device__ __forceinline__ void ecur_next(const EnBatch &B, ECur &c) {
-  while (++c.s < 6)
-    if (c.blk[c.s] == c.s) return;
-  if (++c.ob < c.ob1) {
-    // the orbit table's order, P >= Q >= R lexicographic, as an odometer
-    if (c.tl3[2] < c.tl3[1]) ++c.tl3[2];
-    else if (c.tl3[1] < c.tl3[0]) { ++c.tl3[1]; c.tl3[2] = 0; }
-    else { ++c.tl3[0]; c.tl3[1] = 0; c.tl3[2] = 0; }
-    ecur_orbit(c);
-    return;
-  }
-  c.gi += gridDim.x;
-  ecur_item(B, c);
-}
-__device__ __forceinline__ bool ecur_last_of_orbit(const ECur &c) {
-  for (int s2 = c.s + 1; s2 < 6; ++s2)
-    if (c.blk[s2] == s2) return false;
-  return true;
-}
-
-// Issue the three boxes of block load c into staging slot dst (16 KB each):
-// the block (X, Y, Z) of F(i,j,k)[ab,c], F(i,k,j)[ac,b] and F(j,k,i)[bc,a],
-// all stored as [a][b][c]
-__device__ __forceinline__ void ecur_issue(const EnBatch &B, const ECur &c, float *dst, uint64_t *bar) {
-  const EnJob &J = B.job[c.jc];
-  const int X = c.tl3[perm3(c.s, 0)] * NT, Y = c.tl3[perm3(c.s, 1)] * NT, Z = c.tl3[perm3(c.s, 2)] * NT;
-  const int f0 = c.tl * 3;
-  mbar_expect_tx(bar, 3 * NT * NT * NT * 4);
-#pragma unroll
-  for (int g = 0; g < 3; ++g) tma_load_4d(dst + g * NT * NT * NT, &J.ymap, Z, Y, X, f0 + g, bar);
+__device__ __forceinline__ void ff_add2(float &h, float &l, float h2, float l2) {
+  const float s = h + h2, bp = s - h;
+  l += ((h - (s - bp)) + (h2 - bp)) + l2;
+  h = s;
 }
 
 __device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EN_CONSUMERS) : "memory"); }
@@ -584,56 +580,109 @@ __device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, %0;" :: "
 __global__ void __launch_bounds__(EN_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ EnBatch B) {
   extern __shared__ __align__(1024) unsigned char en_raw[];
-  float *Wsm = (float *)(((uintptr_t)en_raw + 1023) & ~(uintptr_t)1023);   // 6 W blocks
-  float *stg = Wsm + 6 * WBLK;                                              // slots x 3 boxes
-  float *gsm = stg + EN_SLOTS * 3 * NT * NT * NT;                           // G tiles [3][6][16][17]
-  float *t1s = gsm + GV_FLOATS;                                             // t1 [3 occ][3 tiles][16]
-  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS];
-  __shared__ double red[EN_CONSUMERS / 32], red5[EN_CONSUMERS / 32];
-  __shared__ volatile int en_ok;
+  float *stg = (float *)(((uintptr_t)en_raw + 1023) & ~(uintptr_t)1023);   // W staging slots [EN_SLOTS][16^3]
+  float *vset = stg + EN_SLOTS * BOXF;                                      // V sets [2][GSET_FLOATS]
+  float *Wsm = vset + 2 * GSET_FLOATS;                                      // padded W blocks [6][WBLK]
+  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS], vfull_bar[2], vempty_bar[2];
+  __shared__ OrbMeta meta[2];
+  __shared__ float red[EN_WARPS][4];
+  __shared__ volatile int en_abort;          // set by a wait that gave up
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int BOXF = NT * NT * NT;
 
   if (tid == 0) {
-    for (int k = 0; k < EN_SLOTS; ++k) { mbar_init(&full_bar[k], 1); mbar_init(&empty_bar[k], 1); }
+    for (int k = 0; k < EN_SLOTS; ++k) { mbar_init(&full_bar[k], 1); mbar_init(&empty_bar[k], EN_WARPS); }
+    for (int k = 0; k < 2; ++k) { mbar_init(&vfull_bar[k], 1); mbar_init(&vempty_bar[k], EN_WARPS); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    en_ok = 1;
+    en_abort = 0;
   }
   __syncthreads();
 
-  ECur cc{};
-  cc.gi = blockIdx.x;
-  cc.jc = 0;
-  ecur_item(B, cc);
-  if (warp == EN_CONSUMERS / 32) {
-    // ------------------------------------------------ the producer warp: block
-    // loads in the consumers' order, each into the next free staging slot
+  if (warp == EN_WARPS) {
+    // ------------------------------------------------ producer: the CTA's walk
     if (lane == 0) {
-      ECur pc = cc;
-      long long k = 0;
+      int ws = 0, vs = 0;                  // next staging slot, next V set
+      uint32_t wpar = 1, vpar = 1;         // parities of their "free" phases (fresh barriers count as free)
+      long long nW = 0, nV = 0;            // loads issued
       bool ok = true;
-      while (ok && pc.valid) {
-        const int slot = (int)(k % EN_SLOTS);
-        const uint32_t a = smem_u32(&empty_bar[slot]);
-        const uint32_t par = (uint32_t)(((k / EN_SLOTS) & 1) ^ 1);
-        for (long long it = 0; !mbar_try(a, par); ++it) {
-          if (it == WAIT_LIMIT || ((it & 255) == 255 && !en_ok)) {
-            if (it == WAIT_LIMIT) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_EMPTY); }
-            ok = false;
-            break;
+      int jc = 0;
+      for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
+        while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
+        const EnJob &J = B.job[jc];
+        const Dims &d = J.d;
+        const long long q = gi - J.item0;
+        const int tl = (int)(q / d.items_per_trip), chunk = (int)(q % d.items_per_trip);
+        const int ob0 = chunk * d.orb_per_item, ob1 = min(d.n_orb, ob0 + d.orb_per_item);
+        const int4 og = J.orb[ob0];                  // the item's first orbit; the next ones follow
+        int tl3[3] = {og.x, og.y, og.z};
+        const int4 tr = J.trip[J.t0 + tl];
+        const int occ[3] = {tr.x, tr.y, tr.z};
+        const double e3 = J.eps[tr.x] + J.eps[tr.y] + J.eps[tr.z];
+        const float eh = (float)e3, el = (float)(e3 - (double)eh);
+        const long long pidx = (long long)(J.t0 + tl) * d.items_per_trip + chunk;
+        for (int ob = ob0; ob < ob1; ++ob) {
+          int blk[6];
+          orbit_blocks(tl3, blk);
+          // the orbit's V set and record
+          if (!mbar_wait(&vempty_bar[vs], vpar, &en_abort, B.err, ERR_TIMEOUT_EMPTY)) { ok = false; break; }
+          OrbMeta &m = meta[vs];
+          m.pidx = pidx;
+          m.eh = eh;
+          m.el = el;
+          m.jc = jc;
+          m.tl = tl;
+          for (int u = 0; u < 3; ++u) m.tl3[u] = tl3[u];
+          for (int s = 0; s < 6; ++s) m.blk[s] = blk[s];
+          m.last = ob + 1 == ob1;
+          m.valid = 1;
+          float *V = vset + (size_t)vs * GSET_FLOATS;
+          mbar_expect_tx(&vfull_bar[vs], GSET_TX);
+          for (int op = 0; op < 3; ++op) {
+            const int p0 = op == 0 ? occ[1] : occ[0], q0 = op == 2 ? occ[1] : occ[2];
+            for (int tp = 0; tp < 6; ++tp) {
+              const int Ut = tl3[tpair_u(tp)] * NT, Wt = tl3[tpair_w(tp)] * NT;
+              float *dst = V + (op * 6 + tp) * NT * NT;
+              if (tpair_swapped(tp)) tma_load_5d(dst, &J.gmap, Ut, p0, Wt, q0, 1, &vfull_bar[vs]);
+              else                   tma_load_5d(dst, &J.gmap, Wt, q0, Ut, p0, 0, &vfull_bar[vs]);
+            }
+            for (int pos = 0; pos < 3; ++pos)
+              tma_load_2d(V + G_FLOATS + (op * 3 + pos) * T1_ROW, &J.tmap, tl3[pos] * NT, occ[op], &vfull_bar[vs]);
           }
-          if ((it & 255) == 255) __nanosleep(64);
+          ++nV;
+          if (++vs == 2) { vs = 0; vpar ^= 1u; }
+          // the orbit's distinct W blocks, in the order of their permutation index
+          for (int s = 0; s < 6 && ok; ++s) {
+            if (blk[s] != s) continue;
+            if (!mbar_wait(&empty_bar[ws], wpar, &en_abort, B.err, ERR_TIMEOUT_EMPTY)) { ok = false; break; }
+            mbar_expect_tx(&full_bar[ws], BOXF * 4);
+            tma_load_4d(stg + (size_t)ws * BOXF, &J.ymap, tl3[perm3(s, 2)] * NT, tl3[perm3(s, 1)] * NT,
+                        tl3[perm3(s, 0)] * NT, tl, &full_bar[ws]);
+            ++nW;
+            if (++ws == EN_SLOTS) { ws = 0; wpar ^= 1u; }
+          }
+          // the orbit table's order, P >= Q >= R lexicographic, as an odometer
+          if (tl3[2] < tl3[1]) ++tl3[2];
+          else if (tl3[1] < tl3[0]) { ++tl3[1]; tl3[2] = 0; }
+          else { ++tl3[0]; tl3[1] = 0; tl3[2] = 0; }
         }
-        if (!ok) break;
-        ecur_issue(B, pc, stg + (size_t)slot * 3 * BOXF, &full_bar[slot]);
-        ++k;
-        ecur_next(B, pc);
       }
-      // the last loads land before the CTA may exit (bounded; only the latest
-      // load into each slot can still be in flight)
-      for (long long kk = (k > EN_SLOTS ? k - EN_SLOTS : 0); kk < k; ++kk) {
-        const uint32_t a = smem_u32(&full_bar[kk % EN_SLOTS]);
-        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((kk / EN_SLOTS) & 1)); ++it)
+      // end of the walk: a record with valid = 0 (its set's previous load has
+      // been consumed once the set is free again)
+      if (ok && mbar_wait(&vempty_bar[vs], vpar, &en_abort, B.err, ERR_TIMEOUT_EMPTY)) {
+        meta[vs].valid = 0;
+        for (int s = 0; s < 6; ++s) meta[vs].blk[s] = -1;
+        mbar_arrive(&vfull_bar[vs]);
+      }
+      // loads still in flight land before the CTA may exit (bounded): the
+      // latest load into each staging slot and the latest V set (the one
+      // before it shares the end record's set, which was free)
+      for (long long k = (nW > EN_SLOTS ? nW - EN_SLOTS : 0); k < nW; ++k) {
+        const uint32_t a = smem_u32(&full_bar[k % EN_SLOTS]);
+        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k / EN_SLOTS) & 1)); ++it)
+          if ((it & 255) == 255) __nanosleep(128);
+      }
+      for (long long k = (nV > (ok ? 1 : 2) ? nV - (ok ? 1 : 2) : 0); k < nV; ++k) {
+        const uint32_t a = smem_u32(&vfull_bar[k & 1]);
+        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k >> 1) & 1)); ++it)
           if ((it & 255) == 255) __nanosleep(128);
       }
     }
@@ -641,178 +690,157 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     __syncthreads();
     return;
   }
-  double acc4 = 0.0, acc5 = 0.0;                     // the W and V parts of E_(T): E[4], E[5]_ST
-  long long seq = 0;
-  while (cc.valid) {
-    const EnJob &J = B.job[cc.jc];
-    const Dims &d = J.d;
-    const int o = d.o, v = d.v;
-    const int slot = (int)(seq % EN_SLOTS);
-    const uint32_t par = (uint32_t)((seq / EN_SLOTS) & 1);
-    const int4 tr = J.trip[J.t0 + cc.tl];
-    const int occ[3] = {tr.x, tr.y, tr.z};
-    // an orbit's first block: load its V inputs (stored below, read by the compute)
-    constexpr int GV_PER = (GV_LOADS + EN_CONSUMERS - 1) / EN_CONSUMERS;
-    float gv[GV_PER];
-    const bool first_block = cc.s == 0;
-    if (first_block) {
+
+  // -------------------------------------------------- consumers
+  // Thread (pr, hf) takes the point row (la, lb) = (pr / 16, pr % 16) of an
+  // orbit and half hf of its c range.  The W and V parts of E_(T) (E[4] and
+  // E[5]_ST) run as float pairs over the item's orbits.
+  const int pr = tid & (NT * NT - 1), hf = tid >> 8;
+  const int la = pr >> 4, lb = pr & 15;
+  float a4h = 0.f, a4l = 0.f, a5h = 0.f, a5l = 0.f;
+  int ws = 0, vs = 0;
+  uint32_t wpar = 0, vpar = 0;
+  while (true) {
+    mbar_wait(&vfull_bar[vs], vpar, &en_abort, B.err, ERR_TIMEOUT_FULL);
+    const OrbMeta &m = meta[vs];
+    const int valid = m.valid, jc = m.jc, last = m.last;
+    const int T0 = m.tl3[0], T1 = m.tl3[1], T2 = m.tl3[2];
+    int blk[6];
 #pragma unroll
-      for (int q = 0; q < GV_PER; ++q) {
-        const int idx = tid + EN_CONSUMERS * q;
-        float val = 0.f;
-        if (idx < 3 * 6 * NT * NT) {
-          const int op = idx / (6 * NT * NT), tp = (idx / (NT * NT)) % 6, u = (idx >> 4) & 15, w = idx & 15;
-          const int pu = (tp < 2) ? tp : (tp < 4 ? (tp == 2 ? 0 : 2) : (tp == 4 ? 1 : 2));
-          const int pw = (tp == 0) ? 1 : (tp == 1 ? 0 : (tp == 2 ? 2 : (tp == 3 ? 0 : (tp == 4 ? 2 : 1))));
-          const int U = cc.tl3[pu] * NT + u, Wc = cc.tl3[pw] * NT + w;
-          const int p0 = op == 0 ? occ[1] : occ[0], q0 = op == 2 ? occ[1] : occ[2];
-          if (U < v && Wc < v) val = __ldg(J.ovovf + (((size_t)p0 * v + U) * o + q0) * v + Wc);
-        } else if (idx < GV_LOADS) {
-          const int e2 = idx - 3 * 6 * NT * NT;
-          const int op = e2 / (3 * NT), tp = (e2 / NT) % 3, l = e2 % NT;
-          const int a = cc.tl3[tp] * NT + l;
-          if (a < v) val = __ldg(J.t1f + occ[op] * v + a);
-        }
-        gv[q] = val;
-      }
-    }
-    // wait for the block's boxes (bounded; a thread that gives up clears en_ok,
-    // which every thread reads after the barrier that ends the repack)
-    {
-      const uint32_t a = smem_u32(&full_bar[slot]);
-      long long it = 0;
-      while (!mbar_try(a, par)) {
-        if (++it == WAIT_LIMIT) { en_ok = 0; atomicCAS(B.err, 0, ERR_TIMEOUT_FULL); break; }
-        if ((it & 255) == 255) __nanosleep(64);
-      }
-    }
-    // W = box 0 + box 1 + box 2 into the padded W block
-    {
-      const float4 *sb = (const float4 *)(stg + (size_t)slot * 3 * BOXF);
-      float *Wb = Wsm + cc.s * WBLK;
+    for (int s = 0; s < 6; ++s) blk[s] = m.blk[s];
+    // the orbit's W blocks into their padded form
+#pragma unroll 1
+    for (int s = 0; s < 6; ++s) {
+      if (blk[s] != s) continue;
+      mbar_wait(&full_bar[ws], wpar, &en_abort, B.err, ERR_TIMEOUT_FULL);
+      const float4 *sb = (const float4 *)(stg + (size_t)ws * BOXF);
+      float *Wb = Wsm + s * WBLK;
 #pragma unroll
       for (int k = 0; k < BOXF / 4 / EN_CONSUMERS; ++k) {
         const int e4 = tid + k * EN_CONSUMERS;            // float4 index: (x, y, z4)
-        const float4 a0 = sb[e4], a1 = sb[BOXF / 4 + e4], a2 = sb[2 * BOXF / 4 + e4];
-        const int x = e4 >> 6, y = (e4 >> 2) & 15, z = (e4 & 3) * 4;
-        float *w = Wb + x * WX + y * WY + z;
-        w[0] = a0.x + a1.x + a2.x;
-        w[1] = a0.y + a1.y + a2.y;
-        w[2] = a0.z + a1.z + a2.z;
-        w[3] = a0.w + a1.w + a2.w;
+        const float4 a0 = sb[e4];
+        float *w = Wb + (e4 >> 6) * WX + ((e4 >> 2) & 15) * WY + (e4 & 3) * 4;
+        w[0] = a0.x;
+        w[1] = a0.y;
+        w[2] = a0.z;
+        w[3] = a0.w;
       }
-      if (first_block) {
-#pragma unroll
-        for (int q = 0; q < GV_PER; ++q) {
-          const int idx = tid + EN_CONSUMERS * q;
-          if (idx < 3 * 6 * NT * NT) gsm[(idx >> 4) * GROW + (idx & 15)] = gv[q];
-          else if (idx < GV_LOADS) t1s[idx - 3 * 6 * NT * NT] = gv[q];
-        }
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty_bar[ws]);      // this warp is done with the slot
+      if (++ws == EN_SLOTS) { ws = 0; wpar ^= 1u; }
     }
-    cons_bar();
-    if (!en_ok) break;
-    if (tid == 0) mbar_arrive(&empty_bar[slot]);       // the slot is free for the producer
-    const bool orbit_done = ecur_last_of_orbit(cc);
-    if (orbit_done) {
-      // energy over the canonical points a >= b >= c of the orbit; threads
-      // (pr, half) take point row (la, lb) and half of its lc range
-      const double eijk = __ldg(J.eps + occ[0]) + __ldg(J.eps + occ[1]) + __ldg(J.eps + occ[2]);
-      const int pr = tid & (NT * NT - 1), hf = tid >> 8;
-      const int la = pr >> 4, lb = pr & 15;
-      const int ga = cc.tl3[0] * NT + la, gb = cc.tl3[1] * NT + lb;
-      if (ga < v && gb < v && ga >= gb) {
-        // D = e_i + e_j + e_k - e_a - e_b - e_c: the row's part in FP64, then
-        // per point in FP32 (all terms of D share a sign for canonical orbital
-        // energies, |D| > 1, so no cancellation is lost)
-        const float dab = (float)(eijk - (__ldg(J.eps + o + ga) + __ldg(J.eps + o + gb)));
-        // V inputs of the row that do not depend on c: t1 at the a and b
-        // positions, G at the position pairs (a, b) and (b, a); per op
-        // 0, 1, 2 = occupied pair (j, k), (i, k), (i, j) for G and i, j, k for t1
-        float ta[3], tb[3], gab[3], gba[3];
+    cons_bar();                                        // W blocks in place; a failed wait shows here
+    if (en_abort || !valid) break;
+    const EnJob &J = B.job[jc];
+    const int o = J.d.o, v = J.d.v;
+    const float *V = vset + (size_t)vs * GSET_FLOATS;
+    const float *G = V, *t1s = V + G_FLOATS;
+    const int ga = T0 * NT + la, gb = T1 * NT + lb;
+    if (ga < v && gb < v && ga >= gb) {
+      // D = e_i + e_j + e_k - e_a - e_b - e_c: the row's part as a float pair,
+      // rounded once, then per point in FP32 (all terms of D share a sign for
+      // canonical orbital energies, |D| > 1, so no cancellation is lost)
+      const int ne = o + v;
+      float dh = m.eh, dl = m.el;
+      ff_add2(dh, dl, -__ldg(J.epsf + o + ga), -__ldg(J.epsf + ne + o + ga));
+      ff_add2(dh, dl, -__ldg(J.epsf + o + gb), -__ldg(J.epsf + ne + o + gb));
+      const float dab = dh + dl;
+      // V inputs of the row that do not depend on c: t1 at the a and b
+      // positions, G at the position pairs (a, b) and (b, a); op 0, 1, 2 =
+      // occupied pair (j, k), (i, k), (i, j) for G and i, j, k for t1
+      float ta[3], tb[3], gab[3], gba[3];
+#pragma unroll
+      for (int op = 0; op < 3; ++op) {
+        ta[op] = t1s[(op * 3 + 0) * T1_ROW + la];
+        tb[op] = t1s[(op * 3 + 1) * T1_ROW + lb];
+        gab[op] = G[(op * 6 + tpair(0, 1)) * NT * NT + la * NT + lb];          // [a][b]
+        gba[op] = G[(op * 6 + tpair(1, 0)) * NT * NT + la * NT + lb];          // [a][b] (swapped tile)
+      }
+      float rowsum4 = 0.f, rowsum5 = 0.f;  // up to 8 points, added into the float pairs once
+      for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
+        const int gc = T2 * NT + lcc;
+        if (gc >= v || gb < gc) continue;
+        const int l3[3] = {la, lb, lcc};
+        float tcc[3], gac[3], gca[3], gbc[3], gcb[3];
 #pragma unroll
         for (int op = 0; op < 3; ++op) {
-          ta[op] = t1s[(op * 3 + 0) * NT + la];
-          tb[op] = t1s[(op * 3 + 1) * NT + lb];
-          gab[op] = gsm[((op * 6 + tpair(0, 1)) * NT + la) * GROW + lb];
-          gba[op] = gsm[((op * 6 + tpair(1, 0)) * NT + lb) * GROW + la];
+          tcc[op] = t1s[(op * 3 + 2) * T1_ROW + lcc];
+          gac[op] = G[(op * 6 + tpair(0, 2)) * NT * NT + la * NT + lcc];        // [a][c]
+          gca[op] = G[(op * 6 + tpair(2, 0)) * NT * NT + lcc * NT + la];        // [c][a]
+          gbc[op] = G[(op * 6 + tpair(1, 2)) * NT * NT + lcc * NT + lb];        // [c][b] (swapped tile)
+          gcb[op] = G[(op * 6 + tpair(2, 1)) * NT * NT + lcc * NT + lb];        // [c][b]
         }
-        float rowsum4 = 0.f, rowsum5 = 0.f;  // up to 8 points, added into acc4 / acc5 in FP64 once
-        for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
-          const int gc = cc.tl3[2] * NT + lcc;
-          if (gc >= v || gb < gc) continue;
-          const int l3[3] = {la, lb, lcc};
-          float tcc[3], gac[3], gca[3], gbc[3], gcb[3];
+        // t1 of op at position pos, G of op at positions (pu, pw)
+        auto tv = [&](int op, int pos) { return pos == 0 ? ta[op] : (pos == 1 ? tb[op] : tcc[op]); };
+        auto gv = [&](int op, int pu, int pw) {
+          return pu == 0 ? (pw == 1 ? gab[op] : gac[op])
+               : pu == 1 ? (pw == 0 ? gba[op] : gbc[op])
+                         : (pw == 0 ? gca[op] : gcb[op]);
+        };
+        float wv[6], vv[6];
 #pragma unroll
-          for (int op = 0; op < 3; ++op) {
-            tcc[op] = t1s[(op * 3 + 2) * NT + lcc];
-            gac[op] = gsm[((op * 6 + tpair(0, 2)) * NT + la) * GROW + lcc];
-            gca[op] = gsm[((op * 6 + tpair(2, 0)) * NT + lcc) * GROW + la];
-            gbc[op] = gsm[((op * 6 + tpair(1, 2)) * NT + lb) * GROW + lcc];
-            gcb[op] = gsm[((op * 6 + tpair(2, 1)) * NT + lcc) * GROW + lb];
-          }
-          // t1 of op at position pos, G of op at positions (pu, pw)
-          auto tv = [&](int op, int pos) { return pos == 0 ? ta[op] : (pos == 1 ? tb[op] : tcc[op]); };
-          auto gv = [&](int op, int pu, int pw) {
-            return pu == 0 ? (pw == 1 ? gab[op] : gac[op])
-                 : pu == 1 ? (pw == 0 ? gba[op] : gbc[op])
-                           : (pw == 0 ? gca[op] : gcb[op]);
-          };
-          float ws[6], vs[6];
-#pragma unroll
-          for (int s = 0; s < 6; ++s) {
-            const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
-            ws[s] = Wsm[cc.blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
-            // V (Eq. 3) at (x, y, z) = positions (p0, p1, p2) of the point:
-            // t_i^x G_jk^yz + t_j^y G_ik^xz + t_k^z G_ij^xy
-            vs[s] = tv(0, p0) * gv(0, p1, p2) + tv(1, p1) * gv(1, p0, p2) + tv(2, p2) * gv(2, p0, p1);
-          }
-          const float se = ws[0] + ws[3] + ws[4];
-          const float so = ws[1] + ws[2] + ws[5];
-          float sumf4 = 0.f, sumf5 = 0.f;
-#pragma unroll
-          for (int s = 0; s < 6; ++s) {
-            const float br = 3.f * ws[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
-            sumf4 = fmaf(ws[s], br, sumf4);
-            sumf5 = fmaf(vs[s], br, sumf5);
-          }
-          const float D = dab - __ldg(J.epsf + o + gc);
-          const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
-          const float rd = __frcp_rn(D);
-          rowsum4 = fmaf(sumf4 * mult, rd, rowsum4);
-          rowsum5 = fmaf(sumf5 * mult, rd, rowsum5);
+        for (int s = 0; s < 6; ++s) {
+          const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
+          wv[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
+          // V (Eq. 3) at (x, y, z) = positions (p0, p1, p2) of the point:
+          // t_i^x G_jk^yz + t_j^y G_ik^xz + t_k^z G_ij^xy
+          vv[s] = tv(0, p0) * gv(0, p1, p2) + tv(1, p1) * gv(1, p0, p2) + tv(2, p2) * gv(2, p0, p1);
         }
-        acc4 += (double)rowsum4;
-        acc5 += (double)rowsum5;
+        const float se = wv[0] + wv[3] + wv[4];
+        const float so = wv[1] + wv[2] + wv[5];
+        float sumf4 = 0.f, sumf5 = 0.f;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          const float br = 3.f * wv[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
+          sumf4 = fmaf(wv[s], br, sumf4);
+          sumf5 = fmaf(vv[s], br, sumf5);
+        }
+        const float D = dab - __ldg(J.epsf + o + gc);
+        const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
+        const float rd = __frcp_rn(D);
+        rowsum4 = fmaf(sumf4 * mult, rd, rowsum4);
+        rowsum5 = fmaf(sumf5 * mult, rd, rowsum5);
       }
-      cons_bar();                            // W is rebuilt by the next orbit
+      ff_add(a4h, a4l, rowsum4);
+      ff_add(a5h, a5l, rowsum5);
     }
-    // next block load; an item ends when the cursor leaves it
-    const long long gi_now = cc.gi;
-    const int t_now = J.t0 + cc.tl;
-    const long long slot_now = (long long)t_now * d.items_per_trip + (cc.gi - J.item0) % d.items_per_trip;
-    double *partial = J.partial;
-    ecur_next(B, cc);
-    ++seq;
-    if (!cc.valid || cc.gi != gi_now) {
-      // the item's partial: fixed-order reduction over the block
+    const long long pidx = m.pidx;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&vempty_bar[vs]);       // this warp is done with the V set
+    if (++vs == 2) { vs = 0; vpar ^= 1u; }
+    if (last) {
+      // the item's partial: fixed-order reduction of the float pairs (warps,
+      // then the 16 warp sums by warp 0), written in FP64
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        acc4 += __shfl_down_sync(0xffffffffu, acc4, off);
-        acc5 += __shfl_down_sync(0xffffffffu, acc5, off);
+        const float h4 = __shfl_down_sync(0xffffffffu, a4h, off), l4 = __shfl_down_sync(0xffffffffu, a4l, off);
+        const float h5 = __shfl_down_sync(0xffffffffu, a5h, off), l5 = __shfl_down_sync(0xffffffffu, a5l, off);
+        ff_add2(a4h, a4l, h4, l4);
+        ff_add2(a5h, a5l, h5, l5);
       }
-      if (lane == 0) { red[warp] = acc4; red5[warp] = acc5; }
-      cons_bar();
-      if (tid == 0) {
-        double tot4 = 0.0, tot5 = 0.0;
+      if (lane == 0) { red[warp][0] = a4h; red[warp][1] = a4l; red[warp][2] = a5h; red[warp][3] = a5l; }
+      cons_bar();                                      // also: Wsm reads done before the next orbit's copies
+      if (warp == 0) {
+        a4h = lane < EN_WARPS ? red[lane][0] : 0.f;
+        a4l = lane < EN_WARPS ? red[lane][1] : 0.f;
+        a5h = lane < EN_WARPS ? red[lane][2] : 0.f;
+        a5l = lane < EN_WARPS ? red[lane][3] : 0.f;
 #pragma unroll
-        for (int wq = 0; wq < EN_CONSUMERS / 32; ++wq) { tot4 += red[wq]; tot5 += red5[wq]; }
-        partial[2 * slot_now] = tot4 + tot5;
-        partial[2 * slot_now + 1] = tot5;
+        for (int off = EN_WARPS / 2; off > 0; off >>= 1) {
+          const float h4 = __shfl_down_sync(0xffffffffu, a4h, off), l4 = __shfl_down_sync(0xffffffffu, a4l, off);
+          const float h5 = __shfl_down_sync(0xffffffffu, a5h, off), l5 = __shfl_down_sync(0xffffffffu, a5l, off);
+          ff_add2(a4h, a4l, h4, l4);
+          ff_add2(a5h, a5l, h5, l5);
+        }
+        if (lane == 0) {
+          const double e4 = (double)a4h + (double)a4l, e5 = (double)a5h + (double)a5l;
+          J.partial[2 * pidx] = e4 + e5;
+          J.partial[2 * pidx + 1] = e5;
+        }
       }
-      cons_bar();
-      acc4 = 0.0;
-      acc5 = 0.0;
+      a4h = a4l = a5h = a5l = 0.f;
+    } else {
+      cons_bar();                                      // Wsm reads done before the next orbit's copies
     }
   }
   __syncthreads();
@@ -899,9 +927,43 @@ __global__ void build_image(int kind, const double *__restrict__ src, SplitGeom 
   }
 }
 
-__global__ void to_f32(const double *__restrict__ in, long long n, float *__restrict__ out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    out[e] = (float)in[e];
+// FP32 copy of a [rows][cols] array with rows ld floats apart (zero beyond cols).
+__global__ void f32_rows(const double *__restrict__ in, long long rows, int cols, int ld, float *__restrict__ out) {
+  const long long n = rows * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ld;
+    const int c = (int)(e - r * ld);
+    out[e] = c < cols ? (float)in[r * cols + c] : 0.f;
+  }
+}
+
+// Float pair of each value: out[e] = fl(x), out[n + e] = fl(x - fl(x)).
+__global__ void f32_hilo(const double *__restrict__ in, int n, float *__restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const float h = (float)in[e];
+    out[e] = h;
+    out[n + e] = (float)(in[e] - (double)h);
+  }
+}
+
+// FP32 (p u|q w) in both orders, rows vc floats long (zero beyond v):
+// out[0][p][u][q][w] = ovov[p][u][q][w], out[1][q][w][p][u] = ovov[p][u][q][w].
+__global__ void ovov_f32(const double *__restrict__ ovov, int o, int v, int vc, float *__restrict__ out) {
+  const long long half = (long long)o * v * o * vc, n = 2 * half;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int h = e >= half;
+    long long r = e - h * half;
+    const int x3 = (int)(r % vc);
+    r /= vc;
+    const int x2 = (int)(r % o);
+    r /= o;
+    const int x1 = (int)(r % v), x0 = (int)(r / v);
+    float val = 0.f;
+    if (x3 < v)
+      val = (float)(h == 0 ? ovov[(((long long)x0 * v + x1) * o + x2) * v + x3]
+                           : ovov[(((long long)x2 * v + x3) * o + x0) * v + x1]);
+    out[e] = val;
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -946,7 +1008,7 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
     WtJob &J = wb.job[j];
     if (J.g.nc > NCMAX || J.g.S != S) return cudaErrorInvalidValue;
     J.item0 = total;
-    total += (long long)J.g.mt * J.nt * 3 * J.g.nch;
+    total += (long long)J.g.mt * J.nt * J.g.nch;
     ncmax = std::max(ncmax, J.g.nc);
   }
   wb.total_items = total;
@@ -978,6 +1040,14 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
 
 int split_tile() { return NT; }
 
+int split_orb_per_item(int o, int v, int S) {
+  const SplitGeom g = split_geom(o, v, S);
+  const long long T = (v + NT - 1) / NT;
+  const long long n_orb = T * (T + 1) * (T + 2) / 6;
+  const long long opi = (long long)g.nb * n_orb / (8LL * 152);
+  return (int)std::max<long long>(1, std::min<long long>(opi, n_orb));
+}
+
 SplitGeom split_geom(int o, int v, int S) {
   SplitGeom g{};
   g.o = o;
@@ -990,9 +1060,10 @@ SplitGeom split_geom(int o, int v, int S) {
   g.nch = (vp + NCMAX - 1) / NCMAX;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
   g.vc = (v + 3) / 4 * 4;
-  // Triplets per block: about 16 W-term items per SM of a 152-SM GPU, at most
-  // 64 and at most the number of triplets.
-  const long long per_trip = 3LL * g.mt * g.nch;
+  // Triplets per block: about 16 W-term items per SM of a 152-SM GPU in each
+  // of the block's three W-term launches, at most 64 and at most the number of
+  // triplets.
+  const long long per_trip = (long long)g.mt * g.nch;
   long long nb = (16LL * 152 + per_trip - 1) / per_trip;
   nb = std::max<long long>(1, std::min<long long>(64, nb));
   const long long ntrip = std::max<long long>(1, (long long)o * (o + 1) * (o + 2) / 6 - o);
@@ -1014,10 +1085,10 @@ SplitLayout split_layout(int o, int v, int S) {
   L.hc2 = take(a_o);
   L.tb = take(b_v);
   L.hb = take(b_o);
-  L.t1f = take((size_t)o * v * 4);
-  L.epsf = take((size_t)(o + v) * 4);
-  L.ovovf = take((size_t)o * v * o * v * 4);
-  L.y = take((size_t)g.nb * 3 * v * v * g.vc * 4);
+  L.t1f = take((size_t)o * g.vc * 4);
+  L.epsf = take((size_t)2 * (o + v) * 4);
+  L.ovovf = take((size_t)2 * o * v * o * g.vc * 4);
+  L.y = take((size_t)g.nb * v * v * g.vc * 4);
   L.total = off;
   return L;
 }
@@ -1032,9 +1103,9 @@ cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, 
   build_image<<<blocks, thr, 0, st>>>(3, in.t2, g, b + L.hc2);
   build_image<<<blocks, thr, 0, st>>>(4, in.t2, g, b + L.tb);
   build_image<<<blocks, thr, 0, st>>>(5, in.ovoo, g, b + L.hb);
-  to_f32<<<blocks, thr, 0, st>>>(in.t1, (long long)g.o * g.v, (float *)(b + L.t1f));
-  to_f32<<<blocks, thr, 0, st>>>(in.eps, (long long)(g.o + g.v), (float *)(b + L.epsf));
-  to_f32<<<blocks, thr, 0, st>>>(in.ovov, (long long)g.o * g.v * g.o * g.v, (float *)(b + L.ovovf));
+  f32_rows<<<blocks, thr, 0, st>>>(in.t1, g.o, g.v, g.vc, (float *)(b + L.t1f));
+  f32_hilo<<<blocks, thr, 0, st>>>(in.eps, g.o + g.v, (float *)(b + L.epsf));
+  ovov_f32<<<blocks, thr, 0, st>>>(in.ovov, g.o, g.v, g.vc, (float *)(b + L.ovovf));
   return cudaGetLastError();
 }
 
@@ -1091,32 +1162,55 @@ cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *
   J.partial = w.partial;
   J.t0 = t0;
   J.nt = nt;
-  // W-term buffer [nt][3][a][b][vc] as (c < v, b < v, a < v, 3 t + F): boxes of
-  // 16^3, zero-filled where an index reaches v
+  // W buffer [nt][a][b][vc] as (c < v, b < v, a < v, t): boxes of 16^3,
+  // zero-filled where an index reaches v
   const SplitGeom &g = L.g;
   EncodeTiled enc = encode_tiled();
   if (!enc) return cudaErrorNotSupported;
   const cuuint64_t rowb = (cuuint64_t)g.vc * 4;
-  const cuuint64_t dims[4] = {(cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)3 * nt};
+  const cuuint64_t dims[4] = {(cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)g.v, (cuuint64_t)nt};
   const cuuint64_t strides[3] = {rowb, rowb * g.v, rowb * g.v * g.v};
   const cuuint32_t box[4] = {NT, NT, NT, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = enc(&J.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)J.y, dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(&J.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)J.y, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // FP32 (p u|q w) in both orders, [h][x0][x1][x2][vc] as (x3 < v, x2 < o,
+  // x1 < v, x0 < o, h): 16 x 16 tiles over (x1, x3)
+  const cuuint64_t gdims[5] = {(cuuint64_t)g.v, (cuuint64_t)g.o, (cuuint64_t)g.v, (cuuint64_t)g.o, 2};
+  const cuuint64_t gstr[4] = {rowb, rowb * g.o, rowb * g.o * g.v, rowb * g.o * g.v * g.o};
+  const cuuint32_t gbox[5] = {NT, 1, NT, 1, 1};
+  const cuuint32_t gestr[5] = {1, 1, 1, 1, 1};
+  r = enc(&J.gmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void *)J.ovovf, gdims, gstr, gbox, gestr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // FP32 t1 [o][vc] as (a < v, i < o): rows of 16
+  const cuuint64_t tdims[2] = {(cuuint64_t)g.v, (cuuint64_t)g.o};
+  const cuuint64_t tstr[1] = {rowb};
+  const cuuint32_t tbox[2] = {NT, 1};
+  const cuuint32_t testr[2] = {1, 1};
+  r = enc(&J.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)J.t1f, tdims, tstr, tbox, testr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t split_block_params(WtBatch &wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
+cudaError_t split_block_params(WtBatch *wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
                                cudaKernelNodeParams *wp, cudaKernelNodeParams *ep) {
   int wgrid = 1, egrid = 1;
   size_t wsmem = 0;
-  cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
+  cudaError_t e = prepare(wb[0], eb, S, num_sms, &wgrid, &egrid, &wsmem);
   if (e != cudaSuccess) return e;
-  switch (S) {
-    case 2: wt_params<2>(wb, wgrid, wsmem, wargs, wp); break;
-    case 3: wt_params<3>(wb, wgrid, wsmem, wargs, wp); break;
-    default: wt_params<4>(wb, wgrid, wsmem, wargs, wp); break;
+  for (int f = 0; f < SPLIT_WT_LAUNCHES; ++f) {
+    if (f > 0) wb[f] = wb[0];
+    for (int j = 0; j < wb[f].njobs; ++j) wb[f].job[j].gsel = f;
+    switch (S) {
+      case 2: wt_params<2>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
+      case 3: wt_params<3>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
+      default: wt_params<4>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
+    }
   }
   eargs[0] = (void *)&eb;
   *ep = cudaKernelNodeParams{};
@@ -1135,12 +1229,16 @@ cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cud
   cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
   if (e != cudaSuccess) return e;
   if (w0 && (e = cudaEventRecord(w0, st)) != cudaSuccess) return e;
-  switch (S) {
-    case 2: tc_wterm_kernel<2><<<wgrid, THREADS, wsmem, st>>>(wb); break;
-    case 3: tc_wterm_kernel<3><<<wgrid, THREADS, wsmem, st>>>(wb); break;
-    default: tc_wterm_kernel<4><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+  // F(i,j,k), F(i,k,j), F(j,k,i) in this order (the batch is copied at each launch)
+  for (int f = 0; f < SPLIT_WT_LAUNCHES; ++f) {
+    for (int j = 0; j < wb.njobs; ++j) wb.job[j].gsel = f;
+    switch (S) {
+      case 2: tc_wterm_kernel<2><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+      case 3: tc_wterm_kernel<3><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+      default: tc_wterm_kernel<4><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (w1 && (e = cudaEventRecord(w1, st)) != cudaSuccess) return e;
   tc_energy_kernel<<<egrid, EN_THREADS, EN_SMEM, st>>>(eb);
   return cudaGetLastError();
