@@ -273,6 +273,9 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = tmem_base_sh;
+  // A launch that follows this one programmatically may start its CTAs as SMs
+  // free up; it waits for this grid's completion before it touches Y.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (warp == 0 || warp >= 10) {
     // ------------------------------------------------------------ bulk-copy producers
@@ -406,6 +409,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
     const uint32_t trow = tbase + ((uint32_t)(32 * quarter) << 16);
     uint32_t aphase = 0;
     bool ok = true;
+    bool dep_done = false;                          // the preceding launch has completed (see below)
     int jc = 0;
     for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
       while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
@@ -463,6 +467,10 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         const int vo = J.g.v, vc = J.g.vc;
         const int row = m * MROWS + lrow;
         if (row >= vo * vo) continue;
+        // Y is written by the preceding F launch (or read by the preceding
+        // energy launch): under a programmatic launch, everything before
+        // this point overlapped that launch's tail
+        if (!dep_done) { asm volatile("griddepcontrol.wait;" ::: "memory"); dep_done = true; }
         const int zb = nci * nc + g0 * 16;              // first column this thread holds
         float *Wf = J.y + (size_t)tl * vo * vo * vc;
         if (g == 0) {
@@ -596,6 +604,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     en_abort = 0;
   }
   __syncthreads();
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (warp == EN_WARPS) {
     // ------------------------------------------------ producer: the CTA's walk
@@ -604,6 +613,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
       uint32_t wpar = 1, vpar = 1;         // parities of their "free" phases (fresh barriers count as free)
       long long nW = 0, nV = 0;            // loads issued
       bool ok = true;
+      bool dep_done = false;               // the launch that wrote Y has completed
       int jc = 0;
       for (long long gi = blockIdx.x; ok && gi < B.total_items; gi += gridDim.x) {
         while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
@@ -653,6 +663,9 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
           for (int s = 0; s < 6 && ok; ++s) {
             if (blk[s] != s) continue;
             if (!mbar_wait(&empty_bar[ws], wpar, &en_abort, B.err, ERR_TIMEOUT_EMPTY)) { ok = false; break; }
+            // under a programmatic launch the V sets above may already be in
+            // flight; Y needs the preceding W-term launch complete
+            if (!dep_done) { asm volatile("griddepcontrol.wait;" ::: "memory"); dep_done = true; }
             mbar_expect_tx(&full_bar[ws], BOXF * 4);
             tma_load_4d(stg + (size_t)ws * BOXF, &J.ymap, tl3[perm3(s, 2)] * NT, tl3[perm3(s, 1)] * NT,
                         tl3[perm3(s, 0)] * NT, tl, &full_bar[ws]);
@@ -1060,12 +1073,14 @@ SplitGeom split_geom(int o, int v, int S) {
   g.nch = (vp + NCMAX - 1) / NCMAX;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
   g.vc = (v + 3) / 4 * 4;
-  // Triplets per block: about 16 W-term items per SM of a 152-SM GPU in each
-  // of the block's three W-term launches, at most 64 and at most the number of
-  // triplets.
+  // Triplets per block: about 64 W-term items per SM of a 152-SM GPU in each
+  // of the block's three W-term launches (fewer, longer launches: less time in
+  // launch tails), at most 256, at most a 4 GB W buffer and at most the number
+  // of triplets.
   const long long per_trip = (long long)g.mt * g.nch;
-  long long nb = (16LL * 152 + per_trip - 1) / per_trip;
-  nb = std::max<long long>(1, std::min<long long>(64, nb));
+  long long nb = (64LL * 152 + per_trip - 1) / per_trip;
+  nb = std::min<long long>(nb, (4LL << 30) / ((long long)v * v * g.vc * 4));
+  nb = std::max<long long>(1, std::min<long long>(256, nb));
   const long long ntrip = std::max<long long>(1, (long long)o * (o + 1) * (o + 2) / 6 - o);
   g.nb = (int)std::min(nb, ntrip);
   return g;
@@ -1229,19 +1244,34 @@ cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cud
   cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
   if (e != cudaSuccess) return e;
   if (w0 && (e = cudaEventRecord(w0, st)) != cudaSuccess) return e;
+  // Programmatic launches: each kernel of the chain may start its CTAs on SMs
+  // that the previous one has left and waits (griddepcontrol.wait) for that
+  // kernel's completion only before it touches Y.
+  cudaLaunchAttribute attr{};
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(wgrid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = wsmem;
   // F(i,j,k), F(i,k,j), F(j,k,i) in this order (the batch is copied at each launch)
   for (int f = 0; f < SPLIT_WT_LAUNCHES; ++f) {
     for (int j = 0; j < wb.njobs; ++j) wb.job[j].gsel = f;
     switch (S) {
-      case 2: tc_wterm_kernel<2><<<wgrid, THREADS, wsmem, st>>>(wb); break;
-      case 3: tc_wterm_kernel<3><<<wgrid, THREADS, wsmem, st>>>(wb); break;
-      default: tc_wterm_kernel<4><<<wgrid, THREADS, wsmem, st>>>(wb); break;
+      case 2: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<2>, wb); break;
+      case 3: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<3>, wb); break;
+      default: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<4>, wb); break;
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
   }
   if (w1 && (e = cudaEventRecord(w1, st)) != cudaSuccess) return e;
-  tc_energy_kernel<<<egrid, EN_THREADS, EN_SMEM, st>>>(eb);
-  return cudaGetLastError();
+  cfg.gridDim = dim3(egrid);
+  cfg.blockDim = dim3(EN_THREADS);
+  cfg.dynamicSmemBytes = EN_SMEM;
+  return cudaLaunchKernelEx(&cfg, tc_energy_kernel, eb);
 }
 
 }  // namespace tc
