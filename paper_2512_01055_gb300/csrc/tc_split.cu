@@ -456,17 +456,19 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         aphase ^= 1u;
         if (!last) continue;
         // The last chain: the row goes into the job's W buffer Y[triplet][a][b][c].
-        // F(i,j,k) stores its row (a, b) contiguously; F(i,k,j) (row (a, c)) and
-        // F(j,k,i) (row (b, c)) add theirs column by column with reductions in
-        // L2 (not read back, so nothing waits on them).  Each W element has one
-        // writer per launch and the launches are ordered, so every element is
-        // the same IEEE sum on every run.  The warp's 32 lanes hold 32
-        // consecutive c, so each column's reductions cover 128 contiguous bytes.
+        // F(i,j,k) stores its row (a, b): the four lanes of a quad first trade
+        // 16-byte chunks (a 4 x 4 transpose in two xor shuffles) so that every
+        // warp store covers 64 contiguous bytes of each of 8 rows.  F(i,k,j)
+        // (row (a, c)) and F(j,k,i) (row (b, c)) add theirs column by column
+        // with reductions in L2 (not read back, so nothing waits on them); the
+        // warp's 32 lanes hold 32 consecutive c, so each column's reductions
+        // cover 128 contiguous bytes.  Each W element has one writer per launch
+        // and the launches are ordered, so every element is the same IEEE sum
+        // on every run.
         int m, tl, g, nci;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
         const int vo = J.g.v, vc = J.g.vc;
         const int row = m * MROWS + lrow;
-        if (row >= vo * vo) continue;
         // Y is written by the preceding F launch (or read by the preceding
         // energy launch): under a programmatic launch, everything before
         // this point overlapped that launch's tail
@@ -474,17 +476,39 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         const int zb = nci * nc + g0 * 16;              // first column this thread holds
         float *Wf = J.y + (size_t)tl * vo * vo * vc;
         if (g == 0) {
-          float *dst = Wf + (size_t)row * vc + zb;
+          const int q = lane & 3;                       // place in the quad
+          const int r0 = row - q;                       // the quad's first row
 #pragma unroll
           for (int gi2 = 0; gi2 < MAXG; ++gi2) {
-            if (gi2 >= my) break;
+            if (gi2 >= my) break;                       // warp-uniform
+            float4 X[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (zb + gi2 * 16 + 4 * e < vo)
-                *(float4 *)(dst + gi2 * 16 + 4 * e) =
-                    make_float4(v[gi2][4 * e], v[gi2][4 * e + 1], v[gi2][4 * e + 2], v[gi2][4 * e + 3]);
+            for (int k = 0; k < 4; ++k)
+              X[k] = make_float4(v[gi2][4 * k], v[gi2][4 * k + 1], v[gi2][4 * k + 2], v[gi2][4 * k + 3]);
+            // lane q held chunk k of row r0 + q; afterwards X[r] = chunk q of row r0 + r
+#pragma unroll
+            for (int b = 2; b >= 1; b >>= 1) {
+              const bool up = (q & b) != 0;
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                if (k & b) continue;
+                const float4 snd = up ? X[k] : X[k | b];
+                float4 rcv;
+                rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, b);
+                rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, b);
+                rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, b);
+                rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, b);
+                if (up) X[k] = rcv;
+                else X[k | b] = rcv;
+              }
+            }
+            const int col = zb + gi2 * 16 + 4 * q;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+              if (r0 + r < vo * vo && col < vo) *(float4 *)(Wf + (size_t)(r0 + r) * vc + col) = X[r];
           }
         } else {
+          if (row >= vo * vo) continue;
           const int p = row / vo, c = row - p * vo;
           const size_t st = (g == 1) ? (size_t)vc : (size_t)vo * vc;
           float *dst = Wf + ((g == 1) ? (size_t)p * vo * vc : (size_t)p * vc) + c + (size_t)zb * st;
@@ -769,19 +793,33 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         gab[op] = G[(op * 6 + tpair(0, 1)) * NT * NT + la * NT + lb];          // [a][b]
         gba[op] = G[(op * 6 + tpair(1, 0)) * NT * NT + la * NT + lb];          // [a][b] (swapped tile)
       }
+      // This thread's 8 points (la, lb, lc0 + u): every shared read below is a
+      // row base plus a compile-time offset in u.
+      const int lc0 = hf * 8;
+      const float *tcp = t1s + 2 * T1_ROW + lc0;                        // t1 at the c position
+      const float *gacp = G + tpair(0, 2) * NT * NT + la * NT + lc0;   // [a][c]
+      const float *gcap = G + tpair(2, 0) * NT * NT + lc0 * NT + la;   // [c][a]
+      const float *gbcp = G + tpair(1, 2) * NT * NT + lc0 * NT + lb;   // [c][b] (swapped tile)
+      const float *gcbp = G + tpair(2, 1) * NT * NT + lc0 * NT + lb;   // [c][b]
+      // W at permutation s of the point: block blk[s], index l3[p0] WX + l3[p1] WY + l3[p2]
+      auto wcoef = [](int s, int pos) { return perm3(s, 0) == pos ? WX : (perm3(s, 1) == pos ? WY : 1); };
+      int wo[6];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) wo[s] = blk[s] * WBLK + la * wcoef(s, 0) + lb * wcoef(s, 1) + lc0 * wcoef(s, 2);
+      const float *ecp = J.epsf + o + T2 * NT + lc0;
       float rowsum4 = 0.f, rowsum5 = 0.f;  // up to 8 points, added into the float pairs once
-      for (int lcc = hf * 8; lcc < hf * 8 + 8; ++lcc) {
-        const int gc = T2 * NT + lcc;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int gc = T2 * NT + lc0 + u;
         if (gc >= v || gb < gc) continue;
-        const int l3[3] = {la, lb, lcc};
         float tcc[3], gac[3], gca[3], gbc[3], gcb[3];
 #pragma unroll
         for (int op = 0; op < 3; ++op) {
-          tcc[op] = t1s[(op * 3 + 2) * T1_ROW + lcc];
-          gac[op] = G[(op * 6 + tpair(0, 2)) * NT * NT + la * NT + lcc];        // [a][c]
-          gca[op] = G[(op * 6 + tpair(2, 0)) * NT * NT + lcc * NT + la];        // [c][a]
-          gbc[op] = G[(op * 6 + tpair(1, 2)) * NT * NT + lcc * NT + lb];        // [c][b] (swapped tile)
-          gcb[op] = G[(op * 6 + tpair(2, 1)) * NT * NT + lcc * NT + lb];        // [c][b]
+          tcc[op] = tcp[op * 3 * T1_ROW + u];
+          gac[op] = gacp[op * 6 * NT * NT + u];
+          gca[op] = gcap[op * 6 * NT * NT + u * NT];
+          gbc[op] = gbcp[op * 6 * NT * NT + u * NT];
+          gcb[op] = gcbp[op * 6 * NT * NT + u * NT];
         }
         // t1 of op at position pos, G of op at positions (pu, pw)
         auto tv = [&](int op, int pos) { return pos == 0 ? ta[op] : (pos == 1 ? tb[op] : tcc[op]); };
@@ -794,21 +832,27 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
           const int p0 = perm3(s, 0), p1 = perm3(s, 1), p2 = perm3(s, 2);
-          wv[s] = Wsm[blk[s] * WBLK + l3[p0] * WX + l3[p1] * WY + l3[p2]];
+          wv[s] = Wsm[wo[s] + u * wcoef(s, 2)];
           // V (Eq. 3) at (x, y, z) = positions (p0, p1, p2) of the point:
           // t_i^x G_jk^yz + t_j^y G_ik^xz + t_k^z G_ij^xy
           vv[s] = tv(0, p0) * gv(0, p1, p2) + tv(1, p1) * gv(1, p0, p2) + tv(2, p2) * gv(2, p0, p1);
         }
-        const float se = wv[0] + wv[3] + wv[4];
-        const float so = wv[1] + wv[2] + wv[5];
-        float sumf4 = 0.f, sumf5 = 0.f;
+        // The Eq. 1 bracket at permutation s is 3 w_s + (se - 2 so) for even s
+        // and 3 w_s + (so - 2 se) for odd s (se, so: sums of w over the even and
+        // odd permutations), so
+        //   sum_s w_s br_s = 3 sum_s w_s^2 + se^2 + so^2 - 4 se so,
+        //   sum_s v_s br_s = 3 sum_s v_s w_s + ve (se - 2 so) + vo (so - 2 se).
+        const float se = wv[0] + wv[3] + wv[4], so = wv[1] + wv[2] + wv[5];
+        const float ve = vv[0] + vv[3] + vv[4], vo = vv[1] + vv[2] + vv[5];
+        float ww = wv[0] * wv[0], vw = vv[0] * wv[0];
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-          const float br = 3.f * wv[s] + (perm3_even(s) ? se - 2.f * so : so - 2.f * se);
-          sumf4 = fmaf(wv[s], br, sumf4);
-          sumf5 = fmaf(vv[s], br, sumf5);
+        for (int s = 1; s < 6; ++s) {
+          ww = fmaf(wv[s], wv[s], ww);
+          vw = fmaf(vv[s], wv[s], vw);
         }
-        const float D = dab - __ldg(J.epsf + o + gc);
+        const float sumf4 = fmaf(3.f, ww, fmaf(se, se - 4.f * so, so * so));
+        const float sumf5 = fmaf(3.f, vw, fmaf(ve, se - 2.f * so, vo * (so - 2.f * se)));
+        const float D = dab - __ldg(ecp + u);
         const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
         const float rd = __frcp_rn(D);
         rowsum4 = fmaf(sumf4 * mult, rd, rowsum4);
