@@ -186,8 +186,8 @@ def serving(args):
     torch.cuda.set_device(0)
     tcbuild.build()
     reqs, offs = serving_requests(args.requests, args.fp64_share, args.slices)
-    # service-time estimate from the measured single-job rates (FP64 ~0.9 TF/s, split ~100 TF/s at s=3)
-    est = [alg_flops(o, v) / (0.9e12 if p == 0 else 100e12 * 6.0 / (s * (s + 1) / 2)) for (o, v, _, p, s) in reqs]
+    # service-time estimate from the measured single-job rates (FP64 ~0.9 TF/s, split ~130 TF/s at s=3)
+    est = [alg_flops(o, v) / (0.9e12 if p == 0 else 130e12 * 6.0 / (s * (s + 1) / 2)) for (o, v, _, p, s) in reqs]
     capacity = 1.0 / max(1e-9, float(np.mean(est)))
     rate = args.rate if args.rate > 0 else args.load * capacity
     arrivals = offs / rate

@@ -89,6 +89,7 @@ constexpr int EN_WARPS = EN_CONSUMERS / 32;
 constexpr int EN_THREADS = EN_CONSUMERS + 32;   // plus one warp that walks the work and issues the TMA loads
 constexpr int BOXF = NT * NT * NT;        // floats of a 16^3 box
 constexpr int EN_SLOTS = 5;               // W staging slots (one box each)
+constexpr int EN_VSETS = 2;               // V sets (one orbit's G and t1 tiles each)
 constexpr int WX = 273, WY = 17;          // W block index = x*WX + y*WY + z (bank-friendly)
 constexpr int WBLK = 4368;                // floats per W block (>= 15*WX + 15*WY + 16)
 // An orbit's V set: 18 G tiles of 16 x 16 and 9 t1 rows of 16 (each t1 row at
@@ -97,7 +98,7 @@ constexpr int G_FLOATS = 18 * NT * NT;
 constexpr int T1_ROW = 32;
 constexpr int GSET_FLOATS = G_FLOATS + 9 * T1_ROW;
 constexpr int GSET_TX = (G_FLOATS + 9 * NT) * 4;   // bytes the TMA delivers per set
-constexpr int EN_SMEM = 1024 + (EN_SLOTS * BOXF + 2 * GSET_FLOATS + 6 * WBLK) * 4;
+constexpr int EN_SMEM = 1024 + (EN_SLOTS * BOXF + EN_VSETS * GSET_FLOATS + 6 * WBLK) * 4;
 static_assert(EN_SMEM + 1024 <= 232448, "energy kernel shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -613,17 +614,18 @@ __global__ void __launch_bounds__(EN_THREADS, 1)
 tc_energy_kernel(const __grid_constant__ EnBatch B) {
   extern __shared__ __align__(1024) unsigned char en_raw[];
   float *stg = (float *)(((uintptr_t)en_raw + 1023) & ~(uintptr_t)1023);   // W staging slots [EN_SLOTS][16^3]
-  float *vset = stg + EN_SLOTS * BOXF;                                      // V sets [2][GSET_FLOATS]
-  float *Wsm = vset + 2 * GSET_FLOATS;                                      // padded W blocks [6][WBLK]
-  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS], vfull_bar[2], vempty_bar[2];
-  __shared__ OrbMeta meta[2];
+  float *vset = stg + EN_SLOTS * BOXF;                                      // V sets [EN_VSETS][GSET_FLOATS]
+  float *Wsm = vset + EN_VSETS * GSET_FLOATS;                               // padded W blocks [6][WBLK]
+  __shared__ __align__(8) uint64_t full_bar[EN_SLOTS], empty_bar[EN_SLOTS], vfull_bar[EN_VSETS],
+      vempty_bar[EN_VSETS];
+  __shared__ OrbMeta meta[EN_VSETS];
   __shared__ float red[EN_WARPS][4];
   __shared__ volatile int en_abort;          // set by a wait that gave up
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int k = 0; k < EN_SLOTS; ++k) { mbar_init(&full_bar[k], 1); mbar_init(&empty_bar[k], EN_WARPS); }
-    for (int k = 0; k < 2; ++k) { mbar_init(&vfull_bar[k], 1); mbar_init(&vempty_bar[k], EN_WARPS); }
+    for (int k = 0; k < EN_VSETS; ++k) { mbar_init(&vfull_bar[k], 1); mbar_init(&vempty_bar[k], EN_WARPS); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     en_abort = 0;
   }
@@ -682,7 +684,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
               tma_load_2d(V + G_FLOATS + (op * 3 + pos) * T1_ROW, &J.tmap, tl3[pos] * NT, occ[op], &vfull_bar[vs]);
           }
           ++nV;
-          if (++vs == 2) { vs = 0; vpar ^= 1u; }
+          if (++vs == EN_VSETS) { vs = 0; vpar ^= 1u; }
           // the orbit's distinct W blocks, in the order of their permutation index
           for (int s = 0; s < 6 && ok; ++s) {
             if (blk[s] != s) continue;
@@ -710,16 +712,17 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         mbar_arrive(&vfull_bar[vs]);
       }
       // loads still in flight land before the CTA may exit (bounded): the
-      // latest load into each staging slot and the latest V set (the one
-      // before it shares the end record's set, which was free)
+      // latest load into each staging slot and into each V set (after an end
+      // record, not the one into the end record's set, which was free)
       for (long long k = (nW > EN_SLOTS ? nW - EN_SLOTS : 0); k < nW; ++k) {
         const uint32_t a = smem_u32(&full_bar[k % EN_SLOTS]);
         for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k / EN_SLOTS) & 1)); ++it)
           if ((it & 255) == 255) __nanosleep(128);
       }
-      for (long long k = (nV > (ok ? 1 : 2) ? nV - (ok ? 1 : 2) : 0); k < nV; ++k) {
-        const uint32_t a = smem_u32(&vfull_bar[k & 1]);
-        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k >> 1) & 1)); ++it)
+      const long long vfly = ok ? EN_VSETS - 1 : EN_VSETS;
+      for (long long k = (nV > vfly ? nV - vfly : 0); k < nV; ++k) {
+        const uint32_t a = smem_u32(&vfull_bar[k % EN_VSETS]);
+        for (long long it = 0; it < WAIT_LIMIT && !mbar_try(a, (uint32_t)((k / EN_VSETS) & 1)); ++it)
           if ((it & 255) == 255) __nanosleep(128);
       }
     }
@@ -864,7 +867,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     const long long pidx = m.pidx;
     __syncwarp();
     if (lane == 0) mbar_arrive(&vempty_bar[vs]);       // this warp is done with the V set
-    if (++vs == 2) { vs = 0; vpar ^= 1u; }
+    if (++vs == EN_VSETS) { vs = 0; vpar ^= 1u; }
     if (last) {
       // the item's partial: fixed-order reduction of the float pairs (warps,
       // then the 16 warp sums by warp 0), written in FP64
