@@ -44,7 +44,7 @@ struct tc_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   tc::DevBuf ws;                            // tables, partials and sums, reused across calls
-  tc::DevBuf ws_split;                      // BF16 operand images, FP32 copies, W-term buffer
+  tc::DevBuf ws_split;                      // BF16 operand images, FP32 copies, W buffer
   tc::DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies
   double *host_out = nullptr;               // pinned read-back slot
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};     // kernel timing

@@ -90,10 +90,10 @@ struct SplitGeom {
   int mt;                // M tiles: ceil(v^2 / 128)
   int kbv, kbo;          // K blocks over a virtual / an occupied index
   int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
-  int vc;                // innermost extent of the W-term buffer (v rounded up to 4)
-  int nb;                // triplets per block (capacity of the W-term buffer)
+  int vc;                // innermost extent of the W buffer and FP32 copies (v rounded up to 4)
+  int nb;                // triplets per block (capacity of the W buffer)
 };
-// Byte offsets of the operand images, FP32 copies and W-term buffer inside a
+// Byte offsets of the operand images, FP32 copies and W buffer inside a
 // job's split workspace.
 struct SplitLayout {
   SplitGeom g;

@@ -247,7 +247,7 @@ bool Server::run_iteration(int g, std::vector<std::shared_ptr<Req>> &jobs) {
     std::vector<int> still;
     for (int j : open) {
       Req &q = *jobs[j];
-      // split jobs run at most one block of triplets (the W-term buffer) per launch
+      // split jobs run at most one block of triplets (the W buffer) per launch
       const long long cap = g == 0 ? q.units : q.SL.g.nb;
       const long long rem = std::min(q.units - q.next_item, cap) - take[j];
       const long long want = std::max<long long>(1, (long long)(share / q.cost_per_item));
