@@ -52,6 +52,16 @@ def alg_flops(o, v):
     return 2.0 * (o ** 3 * v ** 4 + o ** 4 * v ** 3)
 
 
+def max_over_ranks(x, dist, device):
+    """The job's time is the slowest rank's: MAX all-reduce of one float (x itself when dist is None)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -340,11 +350,7 @@ def main():
             dist.barrier()
         if clk:
             clk.__exit__()
-        t = ev0.elapsed_time(ev1) / 1e3
-        if dist:
-            tt = torch.tensor([t], device=f"cuda:{dev_id}", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, f"cuda:{dev_id}")
         return {"sec": t / steps, "e_t": e_ref, "kernel": statistics.mean(kern), "wterm": statistics.mean(wterm),
                 "prep": statistics.mean(prep),
                 "launches": launches, "clocks": clk.summary() if clk else None}
@@ -374,11 +380,7 @@ def main():
     for _ in range(e2e_steps):
         re = host_step()
         assert re.e_t == head["e_t"]
-    te = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        tt = torch.tensor([te], device=f"cuda:{dev_id}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+    te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, f"cuda:{dev_id}")
 
     bf16_peak, bf16_sus, hbm, src = peaks()
     # the dominant kernel: the fused kernel (FP64) or the W-term GEMMs (split), its
