@@ -88,7 +88,8 @@ void fp64_node_params(const FpBatch &b, int grid, void **args, cudaKernelNodePar
 struct SplitGeom {
   int o, v, S;
   int mt;                // M tiles: ceil(v^2 / 128)
-  int kbv, kbo;          // K blocks over a virtual / an occupied index
+  int kbv, kbo;          // 16-wide blocks over a virtual / an occupied index (kbv sets the N padding)
+  int hv, ho;            // 8-wide K halves over a virtual / an occupied index
   int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
   int vc;                // innermost extent of the W buffer and FP32 copies (v rounded up to 4)
   int nb;                // triplets per block (capacity of the W buffer)

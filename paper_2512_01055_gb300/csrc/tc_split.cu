@@ -68,6 +68,7 @@ constexpr int NT = 16;                    // virtual tile edge of the energy orb
 constexpr int KB = 16;                    // K values per block (one MMA)
 constexpr int MROWS = 128;                // rows of an M tile
 constexpr int A_BLK = MROWS * KB * 2;     // bytes of one A slice block
+constexpr int A_HALF = MROWS * 16;        // bytes of one A slice half (8 K values)
 constexpr int NCMAX = 224;                // widest N chunk
 constexpr int MAXS = 4;
 constexpr int MAX_STAGES = 8;
@@ -141,12 +142,12 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; core matrices of 8 rows
-// x 16 bytes, the next core matrix along K 128 bytes on, the next 8-row group
-// 256 bytes on.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+// x 16 bytes, the next 8-row group 128 bytes on, the next core matrix along K
+// (the block's second K half) lbo bytes on.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;                 // leading byte offset (K direction)
-  d |= (uint64_t)(256 >> 4) << 32;                 // stride byte offset (8-row groups)
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;      // leading byte offset (K direction)
+  d |= (uint64_t)(128 >> 4) << 32;                 // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                          // descriptor version
   return d;                                        // swizzle field 0
 }
@@ -211,35 +212,40 @@ __device__ __forceinline__ void wt_occ(const WtJob &J, int tl, int g, int &p, in
   else             { p = t.y; q = t.z; r = t.x; }
 }
 
-// Sources of K block kc of an item: A block (S slices of 128 x 16) and B block
-// (S slices of nc x 16).  Segments: particle G_p/t_rq, particle G_q/t_rp, hole
-// t_.p/G_rq, hole t_.q/G_rp.
+// Sources of K half h (8 K values) of an item: A half (S slices of 128 rows x
+// 16 bytes) and B half (S slices of nc rows x 16 bytes).  Segments, hv halves
+// over a virtual index or ho over an occupied one: particle G_p/t_rq, particle
+// G_q/t_rp, hole t_.p/G_rq, hole t_.q/G_rp.  seg receives the segment, so the
+// caller can tell whether two halves are consecutive in one image.
 template <int S>
-__device__ __forceinline__ void wt_src(const WtJob &J, int m, int nci, int p, int q, int r, int kc,
+__device__ __forceinline__ void wt_src(const WtJob &J, int m, int nci, int p, int q, int r, int h, int &seg,
                                        const unsigned char *&a, const unsigned char *&b) {
   const SplitGeom &G = J.g;
-  const size_t ablk = (size_t)S * A_BLK, bblk = (size_t)S * G.nc * 32;
-  int kb = kc;
-  if (kb < G.kbv) {
-    a = J.pa + (((size_t)p * G.mt + m) * G.kbv + kb) * ablk;
-    b = J.tb + ((((size_t)r * G.o + q) * G.nch + nci) * G.kbv + kb) * bblk;
+  const size_t ahb = (size_t)S * A_HALF, bhb = (size_t)S * G.nc * 16;
+  if (h < G.hv) {
+    seg = 0;
+    a = J.pa + (((size_t)p * G.mt + m) * G.hv + h) * ahb;
+    b = J.tb + ((((size_t)r * G.o + q) * G.nch + nci) * G.hv + h) * bhb;
     return;
   }
-  kb -= G.kbv;
-  if (kb < G.kbv) {
-    a = J.pa2 + (((size_t)q * G.mt + m) * G.kbv + kb) * ablk;
-    b = J.tb + ((((size_t)r * G.o + p) * G.nch + nci) * G.kbv + kb) * bblk;
+  h -= G.hv;
+  if (h < G.hv) {
+    seg = 1;
+    a = J.pa2 + (((size_t)q * G.mt + m) * G.hv + h) * ahb;
+    b = J.tb + ((((size_t)r * G.o + p) * G.nch + nci) * G.hv + h) * bhb;
     return;
   }
-  kb -= G.kbv;
-  if (kb < G.kbo) {
-    a = J.hc2 + (((size_t)p * G.mt + m) * G.kbo + kb) * ablk;
-    b = J.hb + ((((size_t)r * G.o + q) * G.nch + nci) * G.kbo + kb) * bblk;
+  h -= G.hv;
+  if (h < G.ho) {
+    seg = 2;
+    a = J.hc2 + (((size_t)p * G.mt + m) * G.ho + h) * ahb;
+    b = J.hb + ((((size_t)r * G.o + q) * G.nch + nci) * G.ho + h) * bhb;
     return;
   }
-  kb -= G.kbo;
-  a = J.hc + (((size_t)q * G.mt + m) * G.kbo + kb) * ablk;
-  b = J.hb + ((((size_t)r * G.o + p) * G.nch + nci) * G.kbo + kb) * bblk;
+  h -= G.ho;
+  seg = 3;
+  a = J.hc + (((size_t)q * G.mt + m) * G.ho + h) * ahb;
+  b = J.hb + ((((size_t)r * G.o + p) * G.nch + nci) * G.ho + h) * bhb;
 }
 
 template <int S>
@@ -294,8 +300,8 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         int m, tl, g, nci, p, q, r;
         wt_decode(J, gi - J.item0, m, tl, g, nci);
         wt_occ(J, tl, g, p, q, r);
-        const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
-        const uint32_t abytes = (uint32_t)S * A_BLK, bbytes = (uint32_t)S * J.g.nc * 32;
+        const int nkb = J.g.hv + J.g.ho;                       // 2 (hv + ho) halves, two per K block
+        const uint32_t ahb = (uint32_t)S * A_HALF, bhb = (uint32_t)S * J.g.nc * 16;
         for (int kc = 0; kc < nkb; ++kc, ++seq) {
           const bool mine = rr == pw;
           if (++rr == B.nprod) rr = 0;
@@ -305,17 +311,25 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
               got = mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_EMPTY) ? 1 : 0;
               if (got) {
                 last_seq[pw][stage] = seq;
-                mbar_expect_tx(&full_bar[stage], abytes + bbytes);
+                mbar_expect_tx(&full_bar[stage], 2 * (ahb + bhb));
               }
             }
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) { ok = false; break; }
-            if (lane < 2) {
-              const unsigned char *a, *b;
-              wt_src<S>(J, m, nci, p, q, r, kc, a, b);
-              unsigned char *sA = sm + (size_t)stage * B.slot;
-              if (lane == 0) bulk_load(sA, a, abytes, &full_bar[stage]);
-              else           bulk_load(sA + S * A_BLK, b, bbytes, &full_bar[stage]);
+            // The block's two K halves land S slices apart: [A h0][A h1][B h0][B h1].
+            // Halves of one segment are consecutive in its image (one copy per
+            // operand); a block across a segment boundary takes two.
+            if (lane < 4) {
+              const unsigned char *a0, *b0, *a1, *b1;
+              int s0, s1;
+              wt_src<S>(J, m, nci, p, q, r, 2 * kc, s0, a0, b0);
+              wt_src<S>(J, m, nci, p, q, r, 2 * kc + 1, s1, a1, b1);
+              unsigned char *sA = sm + (size_t)stage * B.slot, *sB = sA + 2 * ahb;
+              const bool one = s0 == s1;
+              if (lane == 0)      bulk_load(sA, a0, one ? 2 * ahb : ahb, &full_bar[stage]);
+              else if (lane == 1) bulk_load(sB, b0, one ? 2 * bhb : bhb, &full_bar[stage]);
+              else if (!one && lane == 2) bulk_load(sA + ahb, a1, ahb, &full_bar[stage]);
+              else if (!one && lane == 3) bulk_load(sB + bhb, b1, bhb, &full_bar[stage]);
             }
             __syncwarp();
           }
@@ -351,10 +365,10 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
         const WtJob &J = B.job[jc];
         const int nc = J.g.nc;
-        const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
+        const int nkb = J.g.hv + J.g.ho;
         const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
         const uint32_t id = idesc(128, nc);
-        const uint32_t bslice = (uint32_t)nc * 32;
+        const uint32_t ahb = (uint32_t)S * A_HALF, bhb = (uint32_t)S * nc * 16;
         for (int ch = 0; ok && ch < nchain; ++ch) {
           const int kc0 = ch * nkb / nchain, kc1 = (ch + 1) * nkb / nchain;
           // A new item needs both accumulators back from the drain; a later
@@ -368,14 +382,14 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
             if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sA = smem_u32(sm + (size_t)stage * B.slot);
-            const uint32_t sB = sA + S * A_BLK;
+            const uint32_t sB = sA + 2 * ahb;
             int n = 0;
 #pragma unroll
             for (int a = 0; a < S; ++a)
 #pragma unroll
               for (int b = 0; b < S - a; ++b) {
                 if (a + b == 0) continue;                                          // levels >= 1 -> L1
-                mma_bf16(tbase + (uint32_t)nc, sdesc(sA + a * A_BLK), sdesc(sB + b * bslice), id,
+                mma_bf16(tbase + (uint32_t)nc, sdesc(sA + a * A_HALF, ahb), sdesc(sB + b * nc * 16, bhb), id,
                          (kc == 0 && n == 0) ? 0u : 1u);
                 ++n;
               }
@@ -383,7 +397,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
               if (!mbar_wait(&accempty_bar, aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            mma_bf16(tbase, sdesc(sA), sdesc(sB), id, kc > kc0 ? 1u : 0u);          // level 0 -> L0
+            mma_bf16(tbase, sdesc(sA, ahb), sdesc(sB, bhb), id, kc > kc0 ? 1u : 0u);  // level 0 -> L0
             mma_commit(&empty_bar[stage]);
             if (++stage == B.stages) { stage = 0; phase ^= 1u; }
           }
@@ -416,7 +430,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
       while (jc + 1 < B.njobs && gi >= B.job[jc + 1].item0) ++jc;
       const WtJob &J = B.job[jc];
       const int nc = J.g.nc;
-      const int nkb = 2 * J.g.kbv + 2 * J.g.kbo;
+      const int nkb = J.g.hv + J.g.ho;
       const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
       const int ng = nc / 16, gsplit = (ng + 1) / 2;
       const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
@@ -908,35 +922,36 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
 
 // ---------------------------------------------------------------- operand images
 
-// One thread per (block, K half, row): reads 8 consecutive K values of one
-// operand row, splits them into S BF16 slices and writes 16 bytes per slice at
-// the row's place in the no-swizzle K-major block.  Rows or K values outside
-// the tensors are zero.
-//   kind 0  A  [p][m][kb]        row (x, y), K f:  (p x | y f)            = ovvv[p][x][y][f]
-//   kind 1  A  [p][m][kb]        row (x, y), K f:  (p y | x f)            = ovvv[p][y][x][f]
-//   kind 2  A  [p][m][kb]        row (x, y), K l:  t_lp^xy = t_pl^yx      = t2[p][l][y][x]
-//   kind 3  A  [p][m][kb]        row (x, y), K l:  t_lp^yx = t_pl^xy      = t2[p][l][x][y]
-//   kind 4  B  [r][q][nc][kb]    row z,      K f:  t_rq^zf                = t2[r][q][z][f]
-//   kind 5  B  [r][q][nc][kb]    row z,      K l:  -(r z | q l)           = -ovoo[r][z][q][l]
+// One thread per (K half, row): reads 8 consecutive K values of one operand
+// row, splits them into S BF16 slices and writes 16 bytes per slice at the
+// row's place in the no-swizzle K-major half (core matrices of 8 rows x 16
+// bytes, 8-row groups 128 bytes apart).  An image is a sequence of halves,
+// each S slices of rows x 16 bytes; rows or K values outside the tensors are
+// zero.
+//   kind 0  A  [p][m][hv]        row (x, y), K f:  (p x | y f)            = ovvv[p][x][y][f]
+//   kind 1  A  [p][m][hv]        row (x, y), K f:  (p y | x f)            = ovvv[p][y][x][f]
+//   kind 2  A  [p][m][ho]        row (x, y), K l:  t_lp^xy = t_pl^yx      = t2[p][l][y][x]
+//   kind 3  A  [p][m][ho]        row (x, y), K l:  t_lp^yx = t_pl^xy      = t2[p][l][x][y]
+//   kind 4  B  [r][q][nc][hv]    row z,      K f:  t_rq^zf                = t2[r][q][z][f]
+//   kind 5  B  [r][q][nc][ho]    row z,      K l:  -(r z | q l)           = -ovoo[r][z][q][l]
 // (kinds 2 and 3 read t_lp^.. as t_pl^.. with the virtual pair swapped, which
 // keeps the reads coalesced).
 __global__ void build_image(int kind, const double *__restrict__ src, SplitGeom G, unsigned char *__restrict__ out) {
   const int o = G.o, v = G.v, S = G.S;
   const bool isA = kind < 4;
   const int rows = isA ? MROWS : G.nc;
-  const int kbx = (kind == 0 || kind == 1 || kind == 4) ? G.kbv : G.kbo;
+  const int nh = (kind == 0 || kind == 1 || kind == 4) ? G.hv : G.ho;
   const int kmax = (kind == 0 || kind == 1 || kind == 4) ? v : o;
-  const long long nblk = isA ? (long long)o * G.mt * kbx : (long long)o * o * G.nch * kbx;
-  const size_t blk_bytes = (size_t)rows * KB * 2;
-  const long long total = nblk * 2 * rows;
+  const long long nhalf = isA ? (long long)o * G.mt * nh : (long long)o * o * G.nch * nh;
+  const size_t half_bytes = (size_t)rows * 16;
+  const long long total = nhalf * rows;
   const long long vv = (long long)v * v;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % rows);
-    const int kh = (int)((e / rows) & 1);
-    const long long blk = e / (2 * rows);
-    const int kb = (int)(blk % kbx);
-    const long long rest = blk / kbx;
-    const int k0 = kb * KB + kh * 8;
+    const long long hb = e / rows;
+    const int h = (int)(hb % nh);
+    const long long rest = hb / nh;
+    const int k0 = h * 8;
     double x[8];
     if (isA) {
       const int m = (int)(rest % G.mt);
@@ -972,9 +987,9 @@ __global__ void build_image(int kind, const double *__restrict__ src, SplitGeom 
         x[u] = val;
       }
     }
-    // position of (row r, K half kh) in the block: core matrix (r/8, kh), row r%8
-    const int off = ((r >> 3) * 2 + kh) * 128 + (r & 7) * 16;
-    unsigned char *base = out + (size_t)blk * S * blk_bytes + off;
+    // position of row r in its half: 8-row group r/8, row r%8
+    const int off = (r >> 3) * 128 + (r & 7) * 16;
+    unsigned char *base = out + (size_t)hb * S * half_bytes + off;
     for (int p = 0; p < S; ++p) {
       __align__(16) __nv_bfloat16 b16[8];
 #pragma unroll
@@ -982,7 +997,7 @@ __global__ void build_image(int kind, const double *__restrict__ src, SplitGeom 
         b16[u] = __double2bfloat16(x[u]);
         x[u] -= (double)__bfloat162float(b16[u]);        // exact FP64 residual
       }
-      *(uint4 *)(base + (size_t)p * blk_bytes) = *(const uint4 *)b16;
+      *(uint4 *)(base + (size_t)p * half_bytes) = *(const uint4 *)b16;
     }
   }
 }
@@ -1116,6 +1131,8 @@ SplitGeom split_geom(int o, int v, int S) {
   g.mt = (int)(((long long)v * v + MROWS - 1) / MROWS);
   g.kbv = (v + KB - 1) / KB;
   g.kbo = (o + KB - 1) / KB;
+  g.hv = (v + 7) / 8;
+  g.ho = (o + 7) / 8;
   const int vp = g.kbv * KB;
   g.nch = (vp + NCMAX - 1) / NCMAX;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
@@ -1137,8 +1154,8 @@ SplitLayout split_layout(int o, int v, int S) {
   SplitLayout L{};
   const SplitGeom g = split_geom(o, v, S);
   L.g = g;
-  const size_t a_v = (size_t)o * g.mt * g.kbv * S * A_BLK, a_o = (size_t)o * g.mt * g.kbo * S * A_BLK;
-  const size_t b_v = (size_t)o * o * g.nch * g.kbv * S * g.nc * 32, b_o = (size_t)o * o * g.nch * g.kbo * S * g.nc * 32;
+  const size_t a_v = (size_t)o * g.mt * g.hv * S * A_HALF, a_o = (size_t)o * g.mt * g.ho * S * A_HALF;
+  const size_t b_v = (size_t)o * o * g.nch * g.hv * S * g.nc * 16, b_o = (size_t)o * o * g.nch * g.ho * S * g.nc * 16;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = (off + bytes + 255) & ~(size_t)255; return r; };
   L.pa = take(a_v);
