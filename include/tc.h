@@ -58,8 +58,10 @@ typedef enum {
 
 typedef enum {
   TC_FP64 = 0,         /* W built with FP64 tensor-core (DMMA) tiles, FP64 everywhere */
-  TC_SPLIT_BF16 = 1    /* W built from BF16 slices on tcgen05 tensor cores, FP32 accumulation,
-                          FP64 denominator, FP64 per-triplet sums and compensated total */
+  TC_SPLIT_BF16 = 1    /* W built from BF16 slices on tcgen05 tensor cores, FP32 accumulation;
+                          D's occupied and (a, b) part as a float pair rounded to FP32, FP32
+                          reciprocal; energies summed in FP32 over <= 8 points, in float pairs
+                          over a work item, in FP64 per triplet, compensated (Neumaier) total */
 } tc_precision;
 
 typedef struct {
@@ -229,7 +231,8 @@ tc_status tc_energy_dev_noalloc(int o, int v, const double *eps, const double *t
                                 double *e_ijk_dev, void *stream, char *errbuf, size_t errlen);
 
 /* Device bytes a job of this shape and precision needs besides its inputs
- * (work tables, partial sums, BF16 slices).  Pure host arithmetic. */
+ * (work tables, partial sums; split path also the BF16 operand images, FP32
+ * copies and the W buffer of one block of triplets).  Pure host arithmetic. */
 size_t tc_workspace_bytes(int o, int v, int prec, int slices);
 
 /* Human-readable name of a status. */
