@@ -99,6 +99,8 @@ typedef struct {
                                 split path, the W-term GEMM launches alone (blocking entry points only) */
   double e_t5;               /* E[5]_ST: the part of E_(T) from the V factor of Eq. 1, sum (V r3(W))/D with the
                                 same weights; E[4] = e_t - e_t5 is the W r3(W)/D part (r3 is the bracket of Eq. 1) */
+  double df_seconds;         /* tc_energy_df_dev: device time of the integral assembly from the DF
+                                factors (gather + three FP64 GEMMs), else 0 */
 } tc_result;
 
 /* Create a context on opt->device (opt may be NULL: device 0, defaults).
@@ -123,6 +125,22 @@ tc_status tc_energy(tc_ctx *ctx, int o, int v, const double *eps, const double *
 tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
                         const double *t2, const tc_ints *ints, int prec, int slices,
                         double *e_ijk_dev, void *stream, tc_result *out);
+
+/* Same as tc_energy_dev with the integrals given as density-fitting (or
+ * Cholesky) factors instead of integral arrays (Eq. 6 of the paper):
+ *   B   DEVICE array [nq][o+v][o+v], B[Q][p][q] with occupied p, q first, so
+ *       that (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s] (Mulliken notation).
+ *   nq  number of factors Q (> 0).
+ * The library assembles (ia|bd), (ia|jl) and (ia|jb) on the device in its own
+ * memory (grow-only, reused by later calls) with FP64 GEMMs, then computes the
+ * energy as tc_energy_dev.  Only B, eps, t1 and t2 cross from the caller.
+ * out->df_seconds is the device time of the assembly; kernel_seconds and
+ * wterm_seconds cover the energy as for tc_energy_dev.  Errors as
+ * tc_energy_dev, plus TC_EINVAL for nq <= 0 or a NULL B, and TC_ENOMEM when
+ * the assembled integrals do not fit the context's budget. */
+tc_status tc_energy_df_dev(tc_ctx *ctx, int o, int v, int nq, const double *eps, const double *t1,
+                           const double *t2, const double *B, int prec, int slices,
+                           double *e_ijk_dev, void *stream, tc_result *out);
 
 /* Weighted contributions of selected occupied triplets (the i >= j >= k
  * regrouping of Eq. 1: E_(T) is the sum over all triplets).  Same inputs as
