@@ -114,9 +114,16 @@ class ClockSampler:
 
 
 def kernel_source_hash(prec):
+    """Hash of the kernel source with comments and blank lines removed (a comment edit keeps it)."""
+    import re
     name = "tc_fp64.cu" if prec == "fp64" else "tc_split.cu"
     p = os.path.join(ROOT, "paper_2512_01055_gb300", "csrc", name)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else None
+    if not os.path.exists(p):
+        return None
+    src = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+    src = "\n".join(line.split("//")[0].rstrip() for line in src.splitlines())
+    src = "\n".join(line for line in src.splitlines() if line.strip())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload, prec):

@@ -41,11 +41,14 @@
 // memory and evaluates the Eq. 1 bracket at the orbit's canonical points,
 // writing FP64 partials (E_(T) and its V part) per item.
 //
-// Operand images.  The slicer writes every operand block of 16 K values
-// directly in the tensor core's K-major no-swizzle layout (8-row x 16-byte
-// core matrices, the two K halves 128 bytes apart, 8-row groups 256 bytes
-// apart), with the s slices of a block contiguous, so a pipeline stage is two
-// contiguous bulk copies (cp.async.bulk): the A block and the B block.
+// Operand images.  The slicer writes the operands directly in the tensor
+// core's K-major no-swizzle layout as a sequence of 8-wide K halves: a half is
+// the s slices of rows x 16 bytes (8-row x 16-byte core matrices, 8-row groups
+// 128 bytes apart).  A K block of 16 is two halves, s slices apart in shared
+// memory (the descriptor's leading byte offset), so a block may take its
+// halves from two segments and a segment is padded to 8 K values, not 16.  A
+// pipeline stage is two contiguous bulk copies (cp.async.bulk), the A halves
+// and the B halves, or four when the block spans a segment boundary.
 //
 // Warp roles of the W-term kernel (384 threads): warps 0, 10 and 11 issue the
 // bulk copies (a warp completes about one stage per ~0.37 us, several warps
