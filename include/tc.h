@@ -142,6 +142,13 @@ tc_status tc_energy_df_dev(tc_ctx *ctx, int o, int v, int nq, const double *eps,
                            const double *t2, const double *B, int prec, int slices,
                            double *e_ijk_dev, void *stream, tc_result *out);
 
+/* Same as tc_energy_df_dev with eps, t1, t2 and B as HOST arrays (copied to
+ * the device, on the context's stream, before the call returns; the caller
+ * keeps ownership).  e_ijk (optional): HOST array [o][o][o] as in tc_energy. */
+tc_status tc_energy_df(tc_ctx *ctx, int o, int v, int nq, const double *eps, const double *t1,
+                       const double *t2, const double *B, int prec, int slices, double *e_ijk,
+                       tc_result *out);
+
 /* Weighted contributions of selected occupied triplets (the i >= j >= k
  * regrouping of Eq. 1: E_(T) is the sum over all triplets).  Same inputs as
  * tc_energy_dev (DEVICE pointers, read in place).

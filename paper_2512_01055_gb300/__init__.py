@@ -19,7 +19,7 @@ TC_FP64, TC_SPLIT_BF16 = 0, 1
 #: Every symbol include/tc.h declares (the CPU test checks the library exports them).
 EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
            "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc", "tc_triplets_dev", "tc_submit", "tc_poll",
-           "tc_wait", "tc_cancel", "tc_serve_stats_get", "tc_inject_fault", "tc_energy_df_dev")
+           "tc_wait", "tc_cancel", "tc_serve_stats_get", "tc_inject_fault", "tc_energy_df_dev", "tc_energy_df")
 TC_JOB_DEVICE_INPUTS = 1
 TC_FAULT_ALLOC, TC_FAULT_STALL = 1, 2
 
@@ -114,6 +114,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_inject_fault.restype = i
     lib.tc_energy_df_dev.argtypes = [vp, i, i, i, vp, vp, vp, vp, i, i, vp, vp, ctypes.POINTER(tc_result)]
     lib.tc_energy_df_dev.restype = i
+    lib.tc_energy_df.argtypes = [vp, i, i, i, vp, vp, vp, vp, i, i, vp, ctypes.POINTER(tc_result)]
+    lib.tc_energy_df.restype = i
     del d, dp
     _lib = lib
     return lib
@@ -210,6 +212,18 @@ def tc_energy_df_dev(ctx, o, v, B, eps, t1, t2, prec=TC_FP64, slices=0, e_ijk=No
     s = load().tc_energy_df_dev(ctx, o, v, int(B.shape[0]), _ptr_dev(eps), _ptr_dev(t1), _ptr_dev(t2), _ptr_dev(B),
                                 prec, slices, _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream),
                                 ctypes.byref(res))
+    _check(ctx, s)
+    return res
+
+
+def tc_energy_df(ctx, o, v, B, eps, t1, t2, prec=TC_FP64, slices=0, e_ijk=None) -> tc_result:
+    """E_(T) from host numpy arrays with the integrals given as DF factors B [nq, o+v, o+v] (occupied first)."""
+    import numpy as np
+    if not (isinstance(B, np.ndarray) and B.ndim == 3 and B.shape[1] == o + v and B.shape[2] == o + v):
+        raise TypeError("B must be a [nq, o+v, o+v] array")
+    res = tc_result()
+    s = load().tc_energy_df(ctx, o, v, int(B.shape[0]), _ptr_np(eps), _ptr_np(t1), _ptr_np(t2), _ptr_np(B), prec,
+                            slices, _ptr_np(e_ijk), ctypes.byref(res))
     _check(ctx, s)
     return res
 

@@ -209,6 +209,59 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   return TC_OK;
 }
 
+// Device bytes tc_energy_df(_dev) holds besides the workspace: the assembled
+// integrals and the gathered factor blocks.
+size_t df_bytes(int o, int v, int nq) {
+  const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
+  const size_t n_b = (size_t)nq * ((size_t)o * v + (size_t)v * v + (size_t)o * o);
+  return sizeof(double) * (n_ovvv + n_ovoo + n_ovov + n_b);
+}
+
+// The integrals from the DF factors B (device) on st, then the energy (Eq. 6,
+// then the path of tc_energy_dev).  Caller holds ctx->mu and checked the
+// arguments and the budget.
+tc_status df_energy(tc_ctx *ctx, int o, int v, int nq, const double *eps, const double *t1, const double *t2,
+                    const double *B, int prec, int slices, double *e_ijk_dev, cudaStream_t st, tc_result *out) {
+  const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
+  const size_t n_b = (size_t)nq * ((size_t)o * v + (size_t)v * v + (size_t)o * o);
+  TC_CUDA(ctx, ctx->in_ovvv.ensure(sizeof(double) * n_ovvv));
+  TC_CUDA(ctx, ctx->in_ovoo.ensure(sizeof(double) * n_ovoo));
+  TC_CUDA(ctx, ctx->in_ovov.ensure(sizeof(double) * n_ovov));
+  TC_CUDA(ctx, ctx->df_b.ensure(sizeof(double) * n_b));
+  for (auto &e : ctx->dfev)
+    if (!e) TC_CUDA(ctx, cudaEventCreate(&e));
+  cublasHandle_t h = (cublasHandle_t)ctx->blas;
+  if (!h) {
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasCreate failed");
+    ctx->blas = h;
+  }
+  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasSetStream failed");
+  double *bov = (double *)ctx->df_b.p, *bvv = bov + (size_t)nq * o * v, *boo = bvv + (size_t)nq * v * v;
+  double *ovvv = (double *)ctx->in_ovvv.p, *ovoo = (double *)ctx->in_ovoo.p, *ovov = (double *)ctx->in_ovov.p;
+  TC_CUDA(ctx, cudaEventRecord(ctx->dfev[0], st));
+  df_gather<<<ctx->num_sms * 8, 256, 0, st>>>(B, nq, o, v, bov, bvv, boo);
+  TC_CUDA(ctx, cudaGetLastError());
+  // (pq|rs) = sum_Q B[Q][pq] B[Q][rs] as products of the blocks (Eq. 6).  A
+  // row-major [rows][cols] result is the column-major cols x rows matrix
+  // X Y^T with X = B_cols (cols x nq) and Y = B_rows (rows x nq).
+  const double one = 1.0, zero = 0.0;
+  const int64_t OV = (int64_t)o * v, VV = (int64_t)v * v, OO = (int64_t)o * o;
+  cublasStatus_t bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, VV, OV, nq, &one, bvv, VV, bov, OV, &zero, ovvv, VV);
+  if (bs == CUBLAS_STATUS_SUCCESS)
+    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OO, OV, nq, &one, boo, OO, bov, OV, &zero, ovoo, OO);
+  if (bs == CUBLAS_STATUS_SUCCESS)
+    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OV, OV, nq, &one, bov, OV, bov, OV, &zero, ovov, OV);
+  if (bs != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasDgemm failed (status %d)", (int)bs);
+  TC_CUDA(ctx, cudaEventRecord(ctx->dfev[1], st));
+  const tc::Inputs in{eps, t1, t2, ovvv, ovoo, ovov};
+  const tc_status s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
+  if (s != TC_OK) return s;
+  float ms = 0.f;
+  TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->dfev[0], ctx->dfev[1]));
+  out->df_seconds = 1e-3 * ms;
+  return TC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -288,6 +341,7 @@ void tc_finalize(tc_ctx *ctx) {
   ctx->in_eps.release(); ctx->in_t1.release(); ctx->in_t2.release();
   ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();
   ctx->df_b.release();
+  ctx->df_in.release();
   if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
   for (auto &e : ctx->dfev) if (e) cudaEventDestroy(e);
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
@@ -323,52 +377,56 @@ tc_status tc_energy_df_dev(tc_ctx *ctx, int o, int v, int nq, const double *eps,
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->err.clear();
   if (nq <= 0 || !B) return fail(ctx, TC_EINVAL, "nq must be positive and B non-NULL (nq=%d)", nq);
-  const tc_ints probe{B, B, B};                       // the integrals are formed below
+  const tc_ints probe{B, B, B};                       // the integrals are formed from B
   tc_status s = check_args(ctx, o, v, eps, t1, t2, &probe, &prec, &slices);
   if (s != TC_OK) return s;
   const auto t0 = std::chrono::steady_clock::now();
   TC_CUDA(ctx, cudaSetDevice(ctx->device));
-  const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
-  const size_t n_b = (size_t)nq * ((size_t)o * v + (size_t)v * v + (size_t)o * o);
-  const size_t need = sizeof(double) * (n_ovvv + n_ovoo + n_ovov + n_b) + tc_workspace_bytes(o, v, prec, slices);
-  if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "job needs %zu B, budget %zu B", need, ctx->budget);
-  cudaStream_t st = (cudaStream_t)stream;
-  TC_CUDA(ctx, ctx->in_ovvv.ensure(sizeof(double) * n_ovvv));
-  TC_CUDA(ctx, ctx->in_ovoo.ensure(sizeof(double) * n_ovoo));
-  TC_CUDA(ctx, ctx->in_ovov.ensure(sizeof(double) * n_ovov));
-  TC_CUDA(ctx, ctx->df_b.ensure(sizeof(double) * n_b));
-  for (auto &e : ctx->dfev)
-    if (!e) TC_CUDA(ctx, cudaEventCreate(&e));
-  cublasHandle_t h = (cublasHandle_t)ctx->blas;
-  if (!h) {
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasCreate failed");
-    ctx->blas = h;
-  }
-  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasSetStream failed");
-  double *bov = (double *)ctx->df_b.p, *bvv = bov + (size_t)nq * o * v, *boo = bvv + (size_t)nq * v * v;
-  double *ovvv = (double *)ctx->in_ovvv.p, *ovoo = (double *)ctx->in_ovoo.p, *ovov = (double *)ctx->in_ovov.p;
-  TC_CUDA(ctx, cudaEventRecord(ctx->dfev[0], st));
-  df_gather<<<ctx->num_sms * 8, 256, 0, st>>>(B, nq, o, v, bov, bvv, boo);
-  TC_CUDA(ctx, cudaGetLastError());
-  // (pq|rs) = sum_Q B[Q][pq] B[Q][rs] as products of the blocks (Eq. 6).  A
-  // row-major [rows][cols] result is the column-major cols x rows matrix
-  // X Y^T with X = B_cols (cols x nq) and Y = B_rows (rows x nq).
-  const double one = 1.0, zero = 0.0;
-  const int64_t OV = (int64_t)o * v, VV = (int64_t)v * v, OO = (int64_t)o * o;
-  cublasStatus_t bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, VV, OV, nq, &one, bvv, VV, bov, OV, &zero, ovvv, VV);
-  if (bs == CUBLAS_STATUS_SUCCESS)
-    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OO, OV, nq, &one, boo, OO, bov, OV, &zero, ovoo, OO);
-  if (bs == CUBLAS_STATUS_SUCCESS)
-    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OV, OV, nq, &one, bov, OV, bov, OV, &zero, ovov, OV);
-  if (bs != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasDgemm failed (status %d)", (int)bs);
-  TC_CUDA(ctx, cudaEventRecord(ctx->dfev[1], st));
-  tc::Inputs in{eps, t1, t2, ovvv, ovoo, ovov};
+  if (df_bytes(o, v, nq) + tc_workspace_bytes(o, v, prec, slices) > ctx->budget)
+    return fail(ctx, TC_ENOMEM, "job needs %zu B, budget %zu B", df_bytes(o, v, nq) + tc_workspace_bytes(o, v, prec, slices),
+                ctx->budget);
   std::memset(out, 0, sizeof *out);
-  s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
+  s = df_energy(ctx, o, v, nq, eps, t1, t2, B, prec, slices, e_ijk_dev, (cudaStream_t)stream, out);
   if (s != TC_OK) return s;
-  float ms = 0.f;
-  TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->dfev[0], ctx->dfev[1]));
-  out->df_seconds = 1e-3 * ms;
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  out->tflops_alg = alg_flops(o, v) / std::max(out->seconds, 1e-12) / 1e12;
+  return TC_OK;
+}
+
+tc_status tc_energy_df(tc_ctx *ctx, int o, int v, int nq, const double *eps, const double *t1, const double *t2,
+                       const double *B, int prec, int slices, double *e_ijk, tc_result *out) {
+  if (!ctx || !out) return TC_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  if (nq <= 0 || !B) return fail(ctx, TC_EINVAL, "nq must be positive and B non-NULL (nq=%d)", nq);
+  const tc_ints probe{B, B, B};
+  tc_status s = check_args(ctx, o, v, eps, t1, t2, &probe, &prec, &slices);
+  if (s != TC_OK) return s;
+  const auto t0 = std::chrono::steady_clock::now();
+  TC_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t n_eps = (size_t)o + v, n_t1 = (size_t)o * v, n_t2 = (size_t)o * o * v * v;
+  const size_t n_b = (size_t)nq * (o + v) * (o + v);
+  const size_t in_bytes = sizeof(double) * (n_eps + (size_t)o * o * o + n_t1 + n_t2 + n_b);
+  const size_t need = in_bytes + df_bytes(o, v, nq) + tc_workspace_bytes(o, v, prec, slices);
+  if (need > ctx->budget) return fail(ctx, TC_ENOMEM, "job needs %zu B, budget %zu B", need, ctx->budget);
+  cudaStream_t st = ctx->stream;
+  TC_CUDA(ctx, ctx->in_eps.ensure(sizeof(double) * (n_eps + (size_t)o * o * o)));
+  TC_CUDA(ctx, ctx->in_t1.ensure(sizeof(double) * n_t1));
+  TC_CUDA(ctx, ctx->in_t2.ensure(sizeof(double) * n_t2));
+  TC_CUDA(ctx, ctx->df_in.ensure(sizeof(double) * n_b));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_eps.p, eps, sizeof(double) * n_eps, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t1.p, t1, sizeof(double) * n_t1, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t2.p, t2, sizeof(double) * n_t2, cudaMemcpyHostToDevice, st));
+  TC_CUDA(ctx, cudaMemcpyAsync(ctx->df_in.p, B, sizeof(double) * n_b, cudaMemcpyHostToDevice, st));
+  double *e_ijk_dev = e_ijk ? (double *)ctx->in_eps.p + n_eps : nullptr;
+  std::memset(out, 0, sizeof *out);
+  s = df_energy(ctx, o, v, nq, (const double *)ctx->in_eps.p, (const double *)ctx->in_t1.p,
+                (const double *)ctx->in_t2.p, (const double *)ctx->df_in.p, prec, slices, e_ijk_dev, st, out);
+  if (s != TC_OK) return s;
+  if (e_ijk) {
+    TC_CUDA(ctx, cudaMemcpyAsync(e_ijk, e_ijk_dev, sizeof(double) * (size_t)o * o * o, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(ctx, cudaStreamSynchronize(st));
+  }
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   out->tflops_alg = alg_flops(o, v) / std::max(out->seconds, 1e-12) / 1e12;
   return TC_OK;

@@ -58,6 +58,18 @@ def test_df_full_size_o20_v200():
     assert np.array_equal(e_df, e_int)
 
 
+@pytest.mark.parametrize("prec,s", [(FP64, 0), (SPLIT, 3)])
+def test_df_host_entry_equals_device_entry(prec, s):
+    """tc_energy_df (host arrays) gives the same bits as tc_energy_df_dev."""
+    amp = synth.make_amplitudes(5, 28, 46)
+    _, r_int, e_int, r_df, e_df = _run(amp, prec, s)
+    e_h = np.zeros((5, 5, 5))
+    r_h = tc.tc_energy_df(gpu_util.context(), 5, 28, np.ascontiguousarray(amp.B), amp.eps, amp.t1, amp.t2,
+                          prec=prec, slices=s, e_ijk=e_h)
+    assert r_h.e_t == r_df.e_t == r_int.e_t
+    assert np.array_equal(e_h, e_df) and r_h.df_seconds > 0.0
+
+
 def test_df_rejects_bad_arguments():
     import torch
     amp = synth.make_amplitudes(3, 8, 45)
