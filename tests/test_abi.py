@@ -54,3 +54,31 @@ def test_null_context_is_rejected(lib):
     assert lib.tc_energy(None, 2, 2, None, None, None, ctypes.byref(ints), 0, 0, None, ctypes.byref(res)) == tc.TC_EINVAL
     lib.tc_finalize(None)
     assert lib.tc_last_error(None) == b""
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets of include/tc.h (compiled with cc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [tc.tc_options, tc.tc_ints, tc.tc_job, tc.tc_serve_stats, tc.tc_result]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tc.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
