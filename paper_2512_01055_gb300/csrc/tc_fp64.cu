@@ -222,15 +222,12 @@ tc_fp64_kernel(const __grid_constant__ FpBatch B) {
 int fp64_tile() { return NT; }
 size_t fp64_smem_bytes() { return sizeof(double) * (size_t)SMEM_DOUBLES; }
 
+// The dynamic shared-memory limit is a per-device attribute of the kernel and
+// exceeds the 48 KB default, so it is set on the current device before every
+// occupancy query and launch (a cheap host-side call; no process-wide flag
+// that would skip it on a second device).
 static cudaError_t configure() {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tc_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fp64_smem_bytes());
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  return cudaSuccess;
+  return cudaFuncSetAttribute(tc_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fp64_smem_bytes());
 }
 
 cudaError_t fp64_blocks_per_sm(int *n) {

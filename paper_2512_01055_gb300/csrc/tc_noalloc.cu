@@ -22,7 +22,9 @@
 // device (with that device current) looks up the device address with
 // cudaGetSymbolAddress and caches it.  That first call also sets the fused
 // kernel's shared-memory attribute, so it should come before any stream
-// capture.
+// capture.  The cached address belongs to the device's primary context: it
+// is valid while that context lives, i.e. as long as nobody resets the device
+// (cudaDeviceReset) and the caller runs in the runtime's primary context.
 #include <cstdio>
 #include <mutex>
 
