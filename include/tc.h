@@ -59,9 +59,9 @@ typedef enum {
 typedef enum {
   TC_FP64 = 0,         /* W built with FP64 tensor-core (DMMA) tiles, FP64 everywhere */
   TC_SPLIT_BF16 = 1    /* W built from BF16 slices on tcgen05 tensor cores, FP32 accumulation;
-                          D's occupied and (a, b) part as a float pair rounded to FP32, FP32
-                          reciprocal; energies summed in FP32 over <= 8 points, in float pairs
-                          over a work item, in FP64 per triplet, compensated (Neumaier) total */
+                          V and the Eq. 1 bracket in FP32; D, 1/D, each point's quotient and
+                          the sums over a work item in float pairs (~48 significant bits);
+                          FP64 per triplet; compensated (Neumaier) FP64 total */
 } tc_precision;
 
 typedef struct {
@@ -165,6 +165,44 @@ tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const do
                           const int *trip, int n, double *e_out, void *stream, tc_result *out);
 
 /* ------------------------------------------------------------------------
+ * One energy over several devices or processes.  The paper hands each GPU a
+ * batch of the work and scales the (T) step over GPUs (Implementation
+ * Details; Results, Figs. 5-6).  Here the units are the occupied triplets
+ * i >= j >= k of the regrouped Eq. 1 (all-equal ones excluded: their
+ * contribution is exactly zero), which are independent of one another and
+ * cost the same; rank r of W takes the contiguous range [n r / W, n (r+1) / W)
+ * of their order (i, j, k) lexicographic.  Each rank needs all the inputs.
+ * The only exchange is one gather of a (sum, compensation) pair per rank,
+ * combined in rank order by tc_combine_parts, so every rank obtains the same
+ * bits whatever the collective's own order.
+ * ------------------------------------------------------------------------ */
+
+/* First triplet (index in the order above) and number of triplets of rank
+ * `rank` of `world` for o occupied orbitals.  Pure host arithmetic.
+ * TC_EINVAL for o <= 0, world <= 0 or rank outside [0, world). */
+tc_status tc_shard_range(int o, int rank, int world, long long *first, long long *count);
+
+/* This rank's share of E_(T): inputs as tc_energy_dev (DEVICE pointers, read
+ * in place, work on `stream`).  part: HOST array [2] that receives the
+ * Neumaier-compensated sum of the range's triplet contributions, in order, as
+ * (sum, compensation); out->e_t = part[0] + part[1].  A rank with an empty
+ * range launches nothing and returns (0, 0).  Errors as tc_energy_dev, plus
+ * TC_EINVAL for an invalid (rank, world). */
+tc_status tc_energy_shard_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1,
+                              const double *t2, const tc_ints *ints, int prec, int slices, int rank,
+                              int world, double *part, void *stream, tc_result *out);
+
+/* (sum, compensation) of n host values x[0..n) in order (Neumaier): part[2].
+ * The rank-local step of tc_energy_shard_dev, for callers that hold the
+ * contributions themselves.  Pure host arithmetic. */
+tc_status tc_sum_parts(const double *x, long long n, double *part);
+
+/* E_(T) from the gathered pairs parts[n][2] of ranks 0 .. n-1: compensated
+ * sum of the sums in rank order plus all compensations.  Pure host
+ * arithmetic; the same inputs give the same bits on every rank. */
+tc_status tc_combine_parts(const double *parts, int n, double *e_t);
+
+/* ------------------------------------------------------------------------
  * Serving: many (T) jobs of uneven (o, v) and mixed precision on one device.
  *
  * tc_submit queues a job and returns at once.  A scheduler owned by the
@@ -250,6 +288,10 @@ tc_status tc_inject_fault(tc_ctx *ctx, int kind, int param);
  * exceed TC_NOALLOC_SCRATCH_BYTES (roughly: more than ~2.5e5 tile orbits).
  * The first call on a device looks up the array's device address and sets
  * the kernel's shared-memory limit; make that call before any stream capture.
+ * The address is then kept per device ordinal for the life of the process:
+ * it belongs to the device's primary context (the one the CUDA runtime uses),
+ * so call this with that context current and do not reset the device
+ * (cudaDeviceReset) between calls.
  * Calls whose GPU work overlaps race on the shared array: serialise them. */
 tc_status tc_energy_dev_noalloc(int o, int v, const double *eps, const double *t1,
                                 const double *t2, const tc_ints *ints, double *e_t_dev,

@@ -19,7 +19,8 @@ TC_FP64, TC_SPLIT_BF16 = 0, 1
 #: Every symbol include/tc.h declares (the CPU test checks the library exports them).
 EXPORTS = ("tc_init", "tc_energy", "tc_energy_dev", "tc_workspace_bytes", "tc_status_str",
            "tc_last_error", "tc_finalize", "tc_energy_dev_noalloc", "tc_triplets_dev", "tc_submit", "tc_poll",
-           "tc_wait", "tc_cancel", "tc_serve_stats_get", "tc_inject_fault", "tc_energy_df_dev", "tc_energy_df")
+           "tc_wait", "tc_cancel", "tc_serve_stats_get", "tc_inject_fault", "tc_energy_df_dev", "tc_energy_df",
+           "tc_shard_range", "tc_energy_shard_dev", "tc_sum_parts", "tc_combine_parts")
 TC_JOB_DEVICE_INPUTS = 1
 TC_FAULT_ALLOC, TC_FAULT_STALL = 1, 2
 
@@ -116,7 +117,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_energy_df_dev.restype = i
     lib.tc_energy_df.argtypes = [vp, i, i, i, vp, vp, vp, vp, i, i, vp, ctypes.POINTER(tc_result)]
     lib.tc_energy_df.restype = i
-    del d, dp
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    lib.tc_shard_range.argtypes = [i, i, i, llp, llp]
+    lib.tc_shard_range.restype = i
+    lib.tc_energy_shard_dev.argtypes = [vp, i, i, vp, vp, vp, ctypes.POINTER(tc_ints), i, i, i, i, dp, vp,
+                                        ctypes.POINTER(tc_result)]
+    lib.tc_energy_shard_dev.restype = i
+    lib.tc_sum_parts.argtypes = [dp, ctypes.c_longlong, dp]
+    lib.tc_sum_parts.restype = i
+    lib.tc_combine_parts.argtypes = [dp, i, dp]
+    lib.tc_combine_parts.restype = i
+    del d
     _lib = lib
     return lib
 
@@ -263,6 +274,55 @@ def tc_energy_dev_noalloc(o, v, eps, t1, t2, ovvv, ovoo, ovov, e_t, e_ijk=None, 
                                      _ptr_dev(e_t), _ptr_dev(e_ijk), ctypes.c_void_p(stream.cuda_stream), buf, 256)
     if s != TC_OK:
         raise TcError(s, buf.value.decode())
+
+
+# ---------------------------------------------------------------------------
+# One energy over several ranks
+# ---------------------------------------------------------------------------
+
+def tc_shard_range(o, rank, world):
+    """(first, count) of rank's contiguous range of the occupied triplets i >= j >= k (all-equal excluded)."""
+    first, count = ctypes.c_longlong(), ctypes.c_longlong()
+    s = load().tc_shard_range(o, rank, world, ctypes.byref(first), ctypes.byref(count))
+    if s != TC_OK:
+        raise TcError(s, f"invalid shard (o={o}, rank={rank}, world={world})")
+    return first.value, count.value
+
+
+def tc_energy_shard_dev(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, rank, world, prec=TC_FP64, slices=0, stream=None):
+    """This rank's (sum, compensation) pair of E_(T) from device tensors; returns (pair, tc_result)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ints = tc_ints(_ptr_dev(ovvv), _ptr_dev(ovoo), _ptr_dev(ovov))
+    part = (ctypes.c_double * 2)()
+    res = tc_result()
+    s = load().tc_energy_shard_dev(ctx, o, v, _ptr_dev(eps), _ptr_dev(t1), _ptr_dev(t2), ctypes.byref(ints), prec,
+                                   slices, rank, world, part, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(res))
+    _check(ctx, s)
+    return (part[0], part[1]), res
+
+
+def tc_sum_parts(x):
+    """(sum, compensation) of the host values x in order."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    part = (ctypes.c_double * 2)()
+    s = load().tc_sum_parts(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size, part)
+    if s != TC_OK:
+        raise TcError(s, "tc_sum_parts")
+    return part[0], part[1]
+
+
+def tc_combine_parts(parts):
+    """E_(T) from the (sum, compensation) pairs of ranks 0 .. n-1."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(parts, dtype=np.float64).reshape(-1, 2))
+    e = ctypes.c_double()
+    s = load().tc_combine_parts(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.shape[0], ctypes.byref(e))
+    if s != TC_OK:
+        raise TcError(s, "tc_combine_parts")
+    return e.value
 
 
 # ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 // points are in tc_serve.cu.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -463,6 +464,81 @@ tc_status tc_triplets_dev(tc_ctx *ctx, int o, int v, const double *eps, const do
   s = run_device(ctx, o, v, in, prec, slices, nullptr, (cudaStream_t)stream, out, &sub, &e_sub);
   if (s != TC_OK) return s;
   for (size_t q = 0; q < where.size(); ++q) e_out[where[q]] = e_sub[q];
+  out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return TC_OK;
+}
+
+// ---------------------------------------------------------------- one energy over several ranks
+
+tc_status tc_shard_range(int o, int rank, int world, long long *first, long long *count) {
+  if (o <= 0 || world <= 0 || rank < 0 || rank >= world || !first || !count) return TC_EINVAL;
+  const long long n = (long long)o * (o + 1) * (o + 2) / 6 - o;   // i >= j >= k, all-equal ones excluded
+  const long long a = n * rank / world, b = n * (rank + 1) / world;
+  *first = a;
+  *count = b - a;
+  return TC_OK;
+}
+
+tc_status tc_sum_parts(const double *x, long long n, double *part) {
+  if (n < 0 || (n > 0 && !x) || !part) return TC_EINVAL;
+  double s = 0.0, c = 0.0;
+  for (long long m = 0; m < n; ++m) {                 // Neumaier's compensated sum, in order
+    const double t = s + x[m];
+    c += (std::fabs(s) >= std::fabs(x[m])) ? ((s - t) + x[m]) : ((x[m] - t) + s);
+    s = t;
+  }
+  part[0] = s;
+  part[1] = c;
+  return TC_OK;
+}
+
+tc_status tc_combine_parts(const double *parts, int n, double *e_t) {
+  if (n < 0 || (n > 0 && !parts) || !e_t) return TC_EINVAL;
+  double s = 0.0, c = 0.0, cc = 0.0;
+  for (int r = 0; r < n; ++r) {                       // rank order: the same bits on every rank
+    const double x = parts[2 * r];
+    const double t = s + x;
+    c += (std::fabs(s) >= std::fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+    cc += parts[2 * r + 1];
+  }
+  *e_t = s + (c + cc);
+  return TC_OK;
+}
+
+tc_status tc_energy_shard_dev(tc_ctx *ctx, int o, int v, const double *eps, const double *t1, const double *t2,
+                              const tc_ints *ints, int prec, int slices, int rank, int world, double *part,
+                              void *stream, tc_result *out) {
+  if (!ctx || !out || !part) return TC_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->err.clear();
+  tc_status s = check_args(ctx, o, v, eps, t1, t2, ints, &prec, &slices);
+  if (s != TC_OK) return s;
+  long long first = 0, count = 0;
+  if (tc_shard_range(o, rank, world, &first, &count) != TC_OK)
+    return fail(ctx, TC_EINVAL, "rank %d of world %d is not a valid shard", rank, world);
+  // the rank's contiguous range of the triplet order (i, j, k) lexicographic
+  std::vector<int4> sub;
+  sub.reserve((size_t)count);
+  long long idx = 0;
+  for (int i = 0; i < o && idx < first + count; ++i)
+    for (int j = 0; j <= i && idx < first + count; ++j)
+      for (int k = 0; k <= j && idx < first + count; ++k) {
+        if (i == k) continue;
+        if (idx >= first) sub.push_back(make_int4(i, j, k, 2 - (i == j) - (j == k)));
+        ++idx;
+      }
+  const auto t0 = std::chrono::steady_clock::now();
+  TC_CUDA(ctx, cudaSetDevice(ctx->device));
+  tc::Inputs in{eps, t1, t2, ints->ovvv, ints->ovoo, ints->ovov};
+  std::memset(out, 0, sizeof *out);
+  std::vector<double> e_sub;
+  if (!sub.empty()) {
+    s = run_device(ctx, o, v, in, prec, slices, nullptr, (cudaStream_t)stream, out, &sub, &e_sub);
+    if (s != TC_OK) return s;
+  }
+  tc_sum_parts(e_sub.data(), (long long)e_sub.size(), part);
+  out->e_t = part[0] + part[1];
   out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return TC_OK;
 }
