@@ -2,26 +2,32 @@
 """Benchmark of the (T) correction: (T) TFLOP/s and seconds per energy.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--prec both|split|fp64] [--slices S]
+                    [--workload NAME] [--prec split|fp64] [--slices S]
 
 A step is one full (T) energy -- every hot-path stage: BF16 slicing into
 tensor-core images (split path), work tables, the W-term GEMM and orbit-energy
 kernels (split path; the FP64 path has one fused W/V/energy kernel), the
 compensated reduction and the read-back of E_T -- on one seeded synthetic job
 whose inputs are resident in HBM before timing starts.  The inputs (ovvv
-alone is 1.28 GB at o=20, v=200) exceed the 129 MB L2, so no L2 flush is
+alone is 20.5 GB at o=40, v=400) exceed the 129 MB L2, so no L2 flush is
 needed between steps.
 
 Headline ("value"): the split-precision path (BF16 slices, s = --slices) on
-the o=20, v=200 workload; beside it ("fp64") the FP64 tensor-core path on the
-same job (fewer steps: one energy takes ~30 s) and |dE| between the two.
+the precision workload o=40, v=400 (Q = 1320).  Beside it: one energy at each
+other slice count (2, 3, 4); the FP64 tensor-core path and every slice count
+on a fixed sample of occupied triplets (tc_triplets_dev, the launch
+configuration of a full run) against the oracle's stored values for the same
+triplets, with the FP64 seconds per energy projected from the sample (one
+full FP64 energy takes about an hour at this size; --fp64-full times one);
+and the same energy end to end through the host entry point.
 
 With N > 1 (torchrun) every rank solves its own copy of the job (independent
 problems, no collective on the data path): weak scaling, value = total
 energies' FLOPs / max-over-ranks time.
 
---impl reference times the CPU oracle (the tests' ground truth) on a bounded
-sample of occupied triplets of the same workload, on this host's cores.
+--impl reference times the CPU oracle (the tests' ground truth) on one seeded
+occupied triplet per step of the same workload, on this host's cores, and
+projects it to the whole energy.
 """
 from __future__ import annotations
 
@@ -137,21 +143,79 @@ def recorded_traffic(kernel, workload, prec):
     return rec.get("dram_bytes_per_launch")
 
 
-def oracle_sample(job, budget_s, seed=4242):
-    """Time oracle.triplet_energy on a seeded sample of triplets; returns (projected s/energy, sample info)."""
+def golden_sample(name):
+    """(triplets, oracle contributions, source) of the stored sample of a workload, or None.
+
+    The values were written by tests/golden/make_golden.py from the oracle only:
+    a fixed sample of occupied triplets for the full-size workloads, every
+    triplet for the o=20 v=200 one (of which the same kind of sample is taken).
+    """
+    g = os.path.join(ROOT, "tests", "golden")
+    p = os.path.join(g, f"sampled_{name}.json")
+    if os.path.exists(p):
+        rec = json.load(open(p))
+        return [tuple(t[:3]) for t in rec["triplets"]], np.array([t[3] for t in rec["triplets"]]), os.path.basename(p)
+    p = os.path.join(g, f"{name}.json")
+    if os.path.exists(p):
+        rec = json.load(open(p))
+        o = rec["o"]
+        want = [(o - 1, o - 2, 0), (o // 2, o // 3, o // 5), (o - 1, o - 1, 1), (o // 2, 2, 2), (1, 0, 0),
+                (o - 1, o // 2, o // 2 - 1)]
+        val = {tuple(t[:3]): t[3] for t in rec["triplets"]}
+        return want, np.array([val[t] for t in want]), os.path.basename(p)
+    return None
+
+
+class CpuMeter:
+    """Wall time and the process's CPU time (all threads) over a region: cores actually used = cpu / wall."""
+
+    def __enter__(self):
+        self.w0, self.c0 = time.perf_counter(), os.times()
+        return self
+
+    def __exit__(self, *a):
+        c1 = os.times()
+        self.wall = time.perf_counter() - self.w0
+        self.cpu = (c1.user - self.c0.user) + (c1.system - self.c0.system)
+
+    @property
+    def cores_used(self):
+        return self.cpu / max(self.wall, 1e-9)
+
+
+def host_job(name, amp=None):
+    """The workload's oracle inputs on the host without the o v^3 array: (amp, job); ovvv slices come per triplet."""
+    o, v = synth.WORKLOADS[name]
+    if amp is None:
+        amp = synth.make_amplitudes(o, v, synth.WORKLOAD_SEEDS[name])
+    job = synth.Job(o=o, v=v, eps=amp.eps, t1=amp.t1, t2=amp.t2, ovvv=None, ovoo=synth.ovoo(amp), ovov=synth.ovov(amp))
+    return amp, job
+
+
+def oracle_triplet_seconds(amp, job, trip):
+    """Time oracle.triplet_energy on one triplet (its ovvv slices are formed before the clock starts)."""
     import oracle
-    trip = [t for t in oracle.triplet_list(job.o) if not (t[0] == t[2])]
-    rng = np.random.default_rng(seed)
-    order = rng.permutation(len(trip))
-    done, t0 = 0, time.perf_counter()
-    while done < len(order):
-        oracle.triplet_energy(job, *trip[order[done]])
+    sl = {x: synth.ovvv_slice(amp, x) for x in set(trip)}
+    with CpuMeter() as m:
+        e = oracle.triplet_energy(job, *trip, ovvv_slices=sl)
+    return e, m
+
+
+def oracle_sample(amp, job, budget_s, seed=4242):
+    """Time the oracle on seeded triplets until budget_s is spent: (projected s/energy, cores used, sample text)."""
+    import oracle
+    trip = [t for t in oracle.triplet_list(job.o) if t[0] != t[2]]
+    order = np.random.default_rng(seed).permutation(len(trip))
+    wall = cpu = 0.0
+    done = 0
+    while done < len(order) and (done == 0 or wall < budget_s):
+        _, m = oracle_triplet_seconds(amp, job, trip[order[done]])
+        wall += m.wall
+        cpu += m.cpu
         done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    proj = el / done * len(trip)
-    return proj, f"{done} of {len(trip)} occupied triplets (oracle.triplet_energy), {el:.1f} s, projected to all"
+    proj = wall / done * len(trip)
+    return proj, cpu / wall, (f"{done} of {len(trip)} occupied triplets (oracle.triplet_energy), {wall:.1f} s, "
+                              f"projected to all")
 
 
 def cores():
@@ -161,22 +225,39 @@ def cores():
         return os.cpu_count()
 
 
+def workload_config(name, args):
+    o, v = synth.WORKLOADS[name]
+    return {"workload": name, "o": o, "v": v, "Q": 3 * (o + v), "prec": args.prec, "slices": args.slices,
+            "l2": ("inputs larger than L2 (ovvv %.2f GB): no flush needed" if 8.0 * o * v ** 3 > 129e6
+                   else "inputs fit in L2 (ovvv %.2f GB): small workload, not timed for a bench line")
+                  % (8.0 * o * v ** 3 / 1e9)}
+
+
 def reference_arm(args, name, o, v, flops, metric):
-    job = synth.workload_job(name)
-    vals = []
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    info = ""
+    """The oracle as it stands, one sampled occupied triplet per step, projected to the whole energy."""
+    import oracle
+    amp, job = host_job(name)
+    trip = [t for t in oracle.triplet_list(o) if t[0] != t[2]]
+    order = np.random.default_rng(4242).permutation(len(trip))
+    walls, used = [], []
     for s in range(args.warmup + args.steps):
-        proj, info = oracle_sample(job, per_step, seed=4242 + s)
+        _, m = oracle_triplet_seconds(amp, job, trip[order[s % len(order)]])
         if s >= args.warmup:
-            vals.append(flops / proj / 1e12)
-    val = statistics.median(vals)
+            walls.append(m.wall)
+            used.append(m.cores_used)
+    per_trip = statistics.mean(walls)
+    val = flops / (per_trip * len(trip)) / 1e12
+    sample = (f"one seeded occupied triplet per step (oracle.triplet_energy), {args.steps} timed steps, "
+              f"mean {per_trip:.2f} s per triplet, projected to all {len(trip)} triplets")
+    cfg = workload_config(name, args)
     print(json.dumps({
         "impl": "reference", "metric": metric, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * flops / (val * 1e12),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_trip,
+        "step": "one sampled occupied triplet", "projected": True,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "o": o, "v": v, "prec": "fp64", "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle", "sample": info},
+        "config": cfg,
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": round(statistics.mean(used), 1),
+                         "cores_available": cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -273,10 +354,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single_o20_v200", choices=sorted(synth.WORKLOADS) + ["serving"])
-    ap.add_argument("--prec", default="both", choices=["both", "split", "fp64"])
+    ap.add_argument("--workload", default="precision_o40_v400", choices=sorted(synth.WORKLOADS) + ["serving"])
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"])
     ap.add_argument("--slices", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-full", action="store_true",
+                    help="also time one full FP64 energy (default only when it takes under a minute)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=24, help="serving: requests of the seeded stream to run")
@@ -286,6 +369,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "serving":
         return serving(args)
+    if args.prec == "fp64":
+        args.slices = 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,12 +401,18 @@ def main():
         torch.cuda.set_device(0)
         tcbuild.build()
     dev_id = torch.cuda.current_device()
+    device = f"cuda:{dev_id}"
 
     head_prec = tc.TC_FP64 if args.prec == "fp64" else tc.TC_SPLIT_BF16
-    head_slices = 0 if head_prec == tc.TC_FP64 else args.slices
-    job = synth.workload_job(name)
+    head_slices = args.slices
+    # inputs: the seeded DF factor and amplitudes drawn on the host, the integral
+    # blocks formed from them on the device (exact: B sits on a 2^-20 grid)
+    t_gen = time.perf_counter()
+    amp = synth.make_amplitudes(o, v, synth.WORKLOAD_SEEDS[name])
+    dev = synth.device_job(amp, device)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
     names = ("eps", "t1", "t2", "ovvv", "ovoo", "ovov")
-    dev = {k: torch.from_numpy(getattr(job, k)).to(f"cuda:{dev_id}") for k in names}
     ctx = tc.tc_init(dev_id)
     stream = torch.cuda.current_stream()
 
@@ -357,18 +448,49 @@ def main():
             dist.barrier()
         if clk:
             clk.__exit__()
-        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, f"cuda:{dev_id}")
-        return {"sec": t / steps, "e_t": e_ref, "kernel": statistics.mean(kern), "wterm": statistics.mean(wterm),
-                "prep": statistics.mean(prep),
-                "launches": launches, "clocks": clk.summary() if clk else None}
+        t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, device)
+        return {"sec": t / steps, "e_t": e_ref, "e_t5": r.e_t5, "kernel": statistics.mean(kern),
+                "wterm": statistics.mean(wterm), "prep": statistics.mean(prep), "launches": launches,
+                "clocks": clk.summary() if clk else None}
 
+    split_counts = (2, 3, 4) if head_prec == tc.TC_SPLIT_BF16 else ()
+    if split_counts:
+        step(head_prec, max(split_counts))      # the largest workspace first: later calls reuse it
     head = timed(head_prec, head_slices, args.warmup, args.steps, True)
+    # the other slice counts: one energy each, same device-side timing
+    per_slices = {}
+    for s in split_counts:
+        r = head if s == head_slices else timed(head_prec, s, 0, 1, False)
+        per_slices[str(s)] = {"s_per_energy": r["sec"], "e_t": r["e_t"], "wterm_ms": 1e3 * r["wterm"],
+                              "tflops": flops / r["sec"] / 1e12}
+
+    # sampled occupied triplets through tc_triplets_dev (the launch configuration of
+    # a full run) against the oracle's stored values for the same triplets
+    sampled = None
+    gs = golden_sample(name)
+    n_trip_all = o * (o + 1) * (o + 2) // 6 - o
+    if gs is not None:
+        trip, ref, src = gs
+        scale = float(np.abs(ref).max())
+        args_t = (ctx, o, v, dev["eps"], dev["t1"], dev["t2"], dev["ovvv"], dev["ovoo"], dev["ovov"], trip)
+        e64, r64 = tc.tc_triplets_dev(*args_t, prec=tc.TC_FP64, stream=stream)
+        sampled = {"triplets": len(trip), "source": src, "oracle_sum": float(ref.sum()),
+                   "fp64": {"max_abs": float(np.abs(e64 - ref).max()),
+                            "max_rel": float(np.abs(e64 - ref).max() / scale),
+                            "s_per_energy_projected": r64.kernel_seconds * n_trip_all / len(trip)}}
+        for s in split_counts:
+            es, _ = tc.tc_triplets_dev(*args_t, prec=head_prec, slices=s, stream=stream)
+            sampled[f"split_s{s}"] = {"max_abs": float(np.abs(es - ref).max()),
+                                      "max_rel": float(np.abs(es - ref).max() / scale),
+                                      "abs_dE_sample_sum": float(abs(es.sum() - ref.sum())),
+                                      "rel_dE_sample_sum": float(abs(es.sum() - ref.sum()) / abs(ref.sum())),
+                                      "abs_dE_vs_fp64_sample_sum": float(abs(es.sum() - e64.sum()))}
+
     # end to end through the host entry point: pinned host inputs -> E_T on the host
-    # (right after the device-timed steps, before the long FP64 run heats the GPU)
     host = {}
     for k in names:
-        pt = torch.empty(getattr(job, k).shape, dtype=torch.float64, pin_memory=True)
-        pt.numpy()[...] = getattr(job, k)
+        pt = torch.empty(dev[k].shape, dtype=torch.float64, pin_memory=True)
+        pt.copy_(dev[k])
         host[k] = pt.numpy()
     h2d = sum(host[k].nbytes for k in names)
 
@@ -379,63 +501,83 @@ def main():
     host_step()
     if dist:
         dist.barrier()
-    e2e_steps = max(1, args.steps)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         re = host_step()
-        assert re.e_t == head["e_t"]
-    te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, f"cuda:{dev_id}")
+        assert re.e_t == head["e_t"], (re.e_t, head["e_t"])
+    te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, device)
+    del host
 
     fp64 = None
-    if args.prec == "both":
-        fp64 = timed(tc.TC_FP64, 0, 1, args.fp64_steps, False)
+    if head_prec != tc.TC_FP64 and (args.fp64_full or flops < 5e13):
+        fp64 = timed(tc.TC_FP64, 0, 1, 1, False)
 
     bf16_peak, bf16_sus, hbm, src = peaks()
-    # the dominant kernel: the fused kernel (FP64) or the W-term GEMMs (split), its
-    # own CUDA-event time summed over its launches inside the timed steps
+    # the dominant kernel: the fused kernel (FP64) or the W-term GEMMs (split), its own
+    # CUDA-event time summed over its launches inside the timed steps.  Its launches run
+    # back to back for the whole energy, so the sustained (power-capped) peak applies.
+    peak_bf16 = bf16_sus or bf16_peak
+    which = "sustained" if bf16_sus else "burst"
     if head_prec == tc.TC_FP64:
         kname, pairs = "tc_fp64_kernel", 1
-        peak = bf16_peak * FP64_NOMINAL_TF / BF16_NOMINAL_TF
-        peak_note = f"FP64 tensor (DMMA) peak = {src} bf16 burst x nominal FP64/BF16 ratio 1.25/2250"
+        peak = peak_bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+        peak_note = f"FP64 tensor (DMMA) peak = {src} bf16 {which} x nominal FP64/BF16 ratio 1.25/2250"
     else:
         kname, pairs = "tc_wterm_kernel", head_slices * (head_slices + 1) // 2
-        peak = bf16_peak
-        peak_note = (f"BF16 dense {src} burst peak; achieved counts the s(s+1)/2 = {pairs} slice-pair products "
-                     f"of the 2(o^3 v^4 + o^4 v^3) flop that form W (padding to tiles not counted)")
+        peak = peak_bf16
+        peak_note = (f"BF16 dense {src} {which} peak (the kernel's launches run back to back through the energy); "
+                     f"achieved counts the s(s+1)/2 = {pairs} slice-pair products of the 2(o^3 v^4 + o^4 v^3) "
+                     f"flop that form W (padding to tiles not counted)")
     achieved = flops * pairs / head["wterm"] / 1e12
     if rank == 0:
+        cfg = workload_config(name, args)
+        cfg.update({"s_per_energy": head["sec"], "e_t": head["e_t"], "e_t5": head["e_t5"],
+                    "prep_ms": 1e3 * head["prep"], "kernels_ms": 1e3 * head["kernel"],
+                    "wterm_ms": 1e3 * head["wterm"], "input_generation_s": t_gen})
+        if head_prec == tc.TC_FP64:
+            dtype = "f64 (DMMA) throughout"
+        else:
+            dtype = (f"bf16x{head_slices} slices -> f32 tensor-core accumulation; epilogue (D, 1/D, quotients, "
+                     f"sums over an item) in float pairs; per-triplet f64; compensated f64 total")
         out = {
             "metric": metric, "value": world * flops / head["sec"] / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * head["sec"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head_prec == tc.TC_FP64 else f"bf16x{head_slices}->f32, f64 denominator+sums",
-            "data": "synthetic (seeded DF integrals and amplitudes)",
-            "config": {"workload": name, "o": o, "v": v, "prec": args.prec, "slices": head_slices,
-                       "s_per_energy": head["sec"], "e_t": head["e_t"], "prep_ms": 1e3 * head["prep"],
-                       "kernels_ms": 1e3 * head["kernel"], "wterm_ms": 1e3 * head["wterm"],
-                       "l2": "inputs larger than L2 (ovvv %.2f GB)" % (job.ovvv.nbytes / 1e9)},
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded DF factor and amplitudes, integrals formed on the device)",
+            "config": cfg,
             "clocks": head["clocks"],
-            "e2e": {"value": world * flops / te / 1e12, "unit": "TFLOP/s", "s_per_energy": te,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+            "e2e": {"value": world * flops / te / 1e12, "unit": "TFLOP/s", "s_per_energy": te, "steps": e2e_steps,
+                    "entry": "tc_energy (host arrays, pinned)", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
             "gpu_launches": head["launches"],
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(kname, name, "fp64" if pairs == 1 else "split"),
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic(kname, name, "fp64" if pairs == 1 else "split"),
                          "kernel": kname, "kernel_ms": 1e3 * head["wterm"], "peak_source": peak_note},
         }
+        if per_slices:
+            out["slices"] = per_slices
+        if sampled:
+            out["sampled"] = sampled
+            fp_s = sampled["fp64"]["s_per_energy_projected"]
+            out["fp64"] = {"s_per_energy": fp_s, "projected": True, "value": flops / fp_s / 1e12, "unit": "TFLOP/s",
+                           "how": "tc_triplets_dev kernel time on the sampled triplets x all triplets / sampled"}
+            out["config"]["speedup_split_vs_fp64"] = fp_s / head["sec"]
         if fp64 is not None:
-            fpeak = bf16_peak * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+            fpeak = peak_bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
             fach = flops / fp64["kernel"] / 1e12
             out["fp64"] = {"value": world * flops / fp64["sec"] / 1e12, "unit": "TFLOP/s", "s_per_energy": fp64["sec"],
-                           "steps": args.fp64_steps, "warmup": 1, "e_t": fp64["e_t"],
+                           "steps": 1, "warmup": 1, "e_t": fp64["e_t"], "projected": False,
                            "roofline": {"bound": "tensor", "achieved": fach, "peak": fpeak, "frac": fach / fpeak,
                                         "kernel": "tc_fp64_kernel"}}
             out["config"]["abs_dE_split_vs_fp64"] = abs(head["e_t"] - fp64["e_t"])
             out["config"]["rel_dE_split_vs_fp64"] = abs(head["e_t"] - fp64["e_t"]) / abs(fp64["e_t"])
             out["config"]["speedup_split_vs_fp64"] = fp64["sec"] / head["sec"]
         if world == 1 and not args.no_cpu_baseline:
-            proj, info = oracle_sample(job, args.cpu_baseline_seconds)
-            out["cpu_baseline"] = {"value": flops / proj / 1e12, "unit": "TFLOP/s", "cores": cores(),
-                                   "kind": "oracle", "sample": info}
+            _, hjob = host_job(name, amp)
+            proj, used, info = oracle_sample(amp, hjob, args.cpu_baseline_seconds)
+            out["cpu_baseline"] = {"value": flops / proj / 1e12, "unit": "TFLOP/s", "cores": round(used, 1),
+                                   "cores_available": cores(), "kind": "oracle", "sample": info, "projected": True}
         print(json.dumps(out))
     tc.tc_finalize(ctx)
     if dist:

@@ -1,7 +1,8 @@
 // Split-precision path: W (Eqs. 2, 5) from BF16 slices on the tcgen05 tensor
-// cores (FP32 accumulation in TMEM), V (Eq. 3) in FP32, D (Fig. 4 sign) in FP64
-// with an FP32 reciprocal, energy terms summed in FP32 over rows of 16 points
-// and in FP64 beyond.
+// cores (FP32 accumulation in TMEM), V (Eq. 3) and the Eq. 1 bracket in FP32;
+// D (Fig. 4 sign), its reciprocal, each point's quotient and the sums over a
+// work item in float pairs (about 48 significant bits, the FP64-class
+// arithmetic of GB300's FP32 pipes); item partials in FP64.
 //
 // Slices.  Every FP64 operand x is written as s BF16 numbers x_0 + ... + x_{s-1}
 // with x_0 = bf16(x) and x_p = bf16(x - x_0 - ... - x_{p-1}) (round to
@@ -613,16 +614,39 @@ struct OrbMeta {
   int valid;           // 0: no more orbits
 };
 
-// Float pair arithmetic (Knuth's TwoSum): h + l carries about 48 bits.
-__device__ __forceinline__ void ff_add(float &h, float &l, float x) {
-  const float s = h + x, bp = s - h;
-  l += (h - (s - bp)) + (x - bp);
-  h = s;
-}
+// Float pair arithmetic: h + l carries about 48 significant bits (Knuth's
+// TwoSum for additions, Dekker's products with an FMA).
 __device__ __forceinline__ void ff_add2(float &h, float &l, float h2, float l2) {
   const float s = h + h2, bp = s - h;
   l += ((h - (s - bp)) + (h2 - bp)) + l2;
   h = s;
+}
+// Renormalise a pair so that |l| <= ulp(h) / 2 (Dekker's fast TwoSum; |h| >= |l|).
+__device__ __forceinline__ void ff_norm(float &h, float &l) {
+  const float s = h + l;
+  l -= s - h;
+  h = s;
+}
+// Reciprocal of the pair (h, l) as a pair: r = fl(1/h) corrected by one Newton
+// step on the exact residual 1 - (h + l) r, formed with FMAs.
+__device__ __forceinline__ void ff_rcp(float h, float l, float &rh, float &rl) {
+  rh = __frcp_rn(h);
+  float e = fmaf(-h, rh, 1.f);
+  e = fmaf(-l, rh, e);
+  rl = rh * e;
+}
+// (h, l) * x as a pair for a float x (Dekker's product with an FMA).
+__device__ __forceinline__ void ff_mulf(float h, float l, float x, float &ph, float &pl) {
+  ph = h * x;
+  pl = fmaf(h, x, -ph) + l * x;
+}
+// (h, l) / 6 as a pair: times the pair of 1/6.
+__device__ __forceinline__ void ff_mul_sixth(float &h, float &l) {
+  constexpr float c_h = 1.f / 6.f;
+  constexpr float c_l = (float)(1.0 / 6.0 - (double)(1.f / 6.f));
+  const float ph = h * c_h;
+  l = fmaf(h, c_h, -ph) + (h * c_l + l * c_h);
+  h = ph;
 }
 
 __device__ __forceinline__ void cons_bar() { asm volatile("bar.sync 1, %0;" :: "n"(EN_CONSUMERS) : "memory"); }
@@ -794,14 +818,13 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
     const float *G = V, *t1s = V + G_FLOATS;
     const int ga = T0 * NT + la, gb = T1 * NT + lb;
     if (ga < v && gb < v && ga >= gb) {
-      // D = e_i + e_j + e_k - e_a - e_b - e_c: the row's part as a float pair,
-      // rounded once, then per point in FP32 (all terms of D share a sign for
-      // canonical orbital energies, |D| > 1, so no cancellation is lost)
+      // D = e_i + e_j + e_k - e_a - e_b - e_c as a float pair (about 48
+      // significant bits): the row's part here, e_c per point below
       const int ne = o + v;
       float dh = m.eh, dl = m.el;
       ff_add2(dh, dl, -__ldg(J.epsf + o + ga), -__ldg(J.epsf + ne + o + ga));
       ff_add2(dh, dl, -__ldg(J.epsf + o + gb), -__ldg(J.epsf + ne + o + gb));
-      const float dab = dh + dl;
+      ff_norm(dh, dl);
       // V inputs of the row that do not depend on c: t1 at the a and b
       // positions, G at the position pairs (a, b) and (b, a); op 0, 1, 2 =
       // occupied pair (j, k), (i, k), (i, j) for G and i, j, k for t1
@@ -827,7 +850,7 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
 #pragma unroll
       for (int s = 0; s < 6; ++s) wo[s] = blk[s] * WBLK + la * wcoef(s, 0) + lb * wcoef(s, 1) + lc0 * wcoef(s, 2);
       const float *ecp = J.epsf + o + T2 * NT + lc0;
-      float rowsum4 = 0.f, rowsum5 = 0.f;  // up to 8 points, added into the float pairs once
+      float r4h = 0.f, r4l = 0.f, r5h = 0.f, r5l = 0.f;   // the row's sums (float pairs)
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int gc = T2 * NT + lc0 + u;
@@ -872,14 +895,24 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
         }
         const float sumf4 = fmaf(3.f, ww, fmaf(se, se - 4.f * so, so * so));
         const float sumf5 = fmaf(3.f, vw, fmaf(ve, se - 2.f * so, vo * (so - 2.f * se)));
-        const float D = dab - __ldg(ecp + u);
-        const float mult = (ga == gc) ? (1.f / 6.f) : ((ga == gb || gb == gc) ? 0.5f : 1.f);
-        const float rd = __frcp_rn(D);
-        rowsum4 = fmaf(sumf4 * mult, rd, rowsum4);
-        rowsum5 = fmaf(sumf5 * mult, rd, rowsum5);
+        // 1/D as a float pair (rh, rl), scaled by the point's share of the
+        // bracket sum: 1 for distinct a > b > c, 1/2 with two equal, 1/6 for a = b = c
+        float Dh = dh, Dl = dl;
+        ff_add2(Dh, Dl, -__ldg(ecp + u), -__ldg(ecp + ne + u));
+        ff_norm(Dh, Dl);
+        float rh, rl;
+        ff_rcp(Dh, Dl, rh, rl);
+        if (ga == gc) ff_mul_sixth(rh, rl);
+        else if (ga == gb || gb == gc) { rh *= 0.5f; rl *= 0.5f; }
+        // the point's two quotients as float pairs, added to the row's pairs
+        float qh, ql;
+        ff_mulf(rh, rl, sumf4, qh, ql);
+        ff_add2(r4h, r4l, qh, ql);
+        ff_mulf(rh, rl, sumf5, qh, ql);
+        ff_add2(r5h, r5l, qh, ql);
       }
-      ff_add(a4h, a4l, rowsum4);
-      ff_add(a5h, a5l, rowsum5);
+      ff_add2(a4h, a4l, r4h, r4l);
+      ff_add2(a5h, a5l, r5h, r5l);
     }
     const long long pidx = m.pidx;
     __syncwarp();

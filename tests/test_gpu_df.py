@@ -16,6 +16,7 @@ import oracle
 import synth
 import paper_2512_01055_gb300 as tc
 from tests import gpu_util
+from tests.split_bounds import split_rel_bound
 
 pytestmark = pytest.mark.gpu
 FP64, SPLIT = tc.TC_FP64, tc.TC_SPLIT_BF16
@@ -44,7 +45,7 @@ def test_df_input_equals_integral_input(o, v, seed, prec, s):
     assert np.array_equal(e_df, e_int)
     assert r_df.df_seconds > 0.0 and r_df.prec == prec
     ref = oracle.energy_by_triplets(job)
-    tol = 1e-9 * abs(ref) if prec == FP64 else 1e-6 * max(1.0, abs(ref)) * (100 if s == 2 else 1)
+    tol = 1e-9 * abs(ref) if prec == FP64 else split_rel_bound(s, o, v) * max(1.0, abs(ref))
     assert abs(r_df.e_t - ref) <= tol
 
 

@@ -19,14 +19,14 @@ import oracle
 import synth
 import paper_2512_01055_gb300 as tc
 from tests import gpu_util
+from tests.split_bounds import split_rel_bound
 
 pytestmark = pytest.mark.gpu
 SPLIT = tc.TC_SPLIT_BF16
-REL = {2: 1e-4, 3: 1e-6, 4: 1e-6}
 
 
-def rel_bound(s, e_ref):
-    return REL[s] * max(1.0, abs(e_ref))
+def rel_bound(s, e_ref, o, v):
+    return split_rel_bound(s, o, v) * max(1.0, abs(e_ref))
 
 
 @pytest.mark.parametrize("s", [2, 3, 4])
@@ -37,10 +37,12 @@ def test_tiny_workload_all_slice_counts(s):
     err = abs(r.e_t - ref)
     print(f"s={s} E={r.e_t:.12e} ref={ref:.12e} |dE|={err:.3e} rel={err / abs(ref):.3e}")
     assert r.prec == SPLIT and r.slices == s
-    assert err <= rel_bound(s, ref)
+    assert err <= rel_bound(s, ref, job.o, job.v)
     scale = max(abs(oracle.triplet_energy(job, *t)) for t in oracle.triplet_list(job.o))
+    worst = max(abs(e_ijk[t] - oracle.triplet_energy(job, *t)) for t in oracle.triplet_list(job.o)) / scale
+    print(f"s={s} worst triplet |de| / max |e| = {worst:.3e}")
     for t in oracle.triplet_list(job.o):
-        assert abs(e_ijk[t] - oracle.triplet_energy(job, *t)) <= 10 * REL[s] * scale, t
+        assert abs(e_ijk[t] - oracle.triplet_energy(job, *t)) <= 10 * split_rel_bound(s, job.o, job.v) * scale, t
 
 
 @pytest.mark.parametrize("o,v,seed", [(3, 5, 1), (4, 17, 2), (5, 33, 3), (2, 47, 4), (7, 20, 5), (3, 64, 6)])
@@ -50,7 +52,7 @@ def test_ragged_shapes(o, v, seed):
     r, e_ijk = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
     ref = oracle.energy_by_triplets(job)
     print(f"o={o} v={v} |dE|/|E|={abs(r.e_t - ref) / abs(ref):.3e}")
-    assert abs(r.e_t - ref) <= rel_bound(3, ref)
+    assert abs(r.e_t - ref) <= rel_bound(3, ref, o, v)
 
 
 def test_physical_scale_twin_absolute_bound():
@@ -112,7 +114,7 @@ def test_invalid_slice_counts():
 @pytest.mark.skipif(not __import__("os").path.exists(__import__("os").path.join(
     __import__("os").path.dirname(__import__("os").path.abspath(__file__)), "golden", "single_o20_v200.json")),
     reason="golden not generated")
-@pytest.mark.parametrize("s", [2, 3])
+@pytest.mark.parametrize("s", [2, 3, 4])
 def test_single_o20_v200_against_stored_oracle(s):
     """The o=20, v=200 workload: E_T and every triplet contribution vs the stored oracle values."""
     import json
@@ -121,7 +123,27 @@ def test_single_o20_v200_against_stored_oracle(s):
     job = synth.workload_job("single_o20_v200")
     r, e_ijk = gpu_util.energy_dev(job, prec=SPLIT, slices=s, want_trip=True)
     print(f"s={s} E={r.e_t:.10e} ref={gold['e_t']:.10e} rel={abs(r.e_t - gold['e_t']) / abs(gold['e_t']):.2e}")
-    assert abs(r.e_t - gold["e_t"]) <= rel_bound(s, gold["e_t"])
+    assert abs(r.e_t - gold["e_t"]) <= rel_bound(s, gold["e_t"], job.o, job.v)
     scale = max(abs(t[3]) for t in gold["triplets"])
     for i, j, k, x in gold["triplets"]:
-        assert abs(e_ijk[i, j, k] - x) <= 10 * REL[s] * scale
+        assert abs(e_ijk[i, j, k] - x) <= 10 * split_rel_bound(s, job.o, job.v) * scale
+
+
+@pytest.mark.skipif(not __import__("os").path.exists(__import__("os").path.join(
+    __import__("os").path.dirname(__import__("os").path.abspath(__file__)), "golden", "single_o20_v200.json")),
+    reason="golden not generated")
+def test_single_o20_v200_physical_twin_absolute_bound():
+    """o=20 v=200 with t1, t2 scaled by mu = 2^-13 (|E_T| ~ 0.09 Eh): the literal 1e-6 Eh bound, full energy."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "single_o20_v200.json")))
+    job = synth.workload_job("single_o20_v200")
+    mu = 2.0 ** -13
+    twin = dataclasses.replace(job, t1=job.t1 * mu, t2=job.t2 * mu)
+    ref = gold["e_t"] * mu * mu                     # exact scaling law (pinned on the oracle)
+    assert 0.01 < abs(ref) < 1.0
+    d = gpu_util.to_device(twin)
+    for s in (3, 4):
+        r, _ = gpu_util.energy_dev(twin, prec=SPLIT, slices=s, dev=d)
+        print(f"twin o=20 v=200 s={s} E={r.e_t:.12e} ref={ref:.12e} |dE|={abs(r.e_t - ref):.3e}")
+        assert abs(r.e_t - ref) <= 1e-6
