@@ -1,21 +1,18 @@
 """Error bounds of the split-precision path used by the parity tests.
 
 s BF16 slices keep the slice-pair products p + q < s of each operand product.
-For s >= 3 the dropped pairs are 2^-24 of the product or smaller, below the
-FP32 accumulation error, and the bound is the stated 1e-6 relative
-(|dE| <= 1e-6 max(1 Eh, |E_T|); literally 1e-6 Eh on the physical-scale twins).
-
-For s = 2 the dropped pairs (x1 y1, x0 y2, x2 y0) are about 2^-16 of each
-product, with random signs.  W sums K = 2v + 2o of them and E_T sums many
-points, so the relative error of E_T falls as v grows: on the tiny
-workloads (v < 64) it is bounded by S2_SMALL, from v = 64 on by 1e-6 like
-s >= 3 (measured: within 2.4e-9 of s = 3 at o=20 v=200).
+The dropped pairs are about 2^-8s of each product with random signs, and W
+sums K = 2v + 2o products accumulated in FP32, whose rounding (about 2^-24
+per addition, partly systematic) dominates the error of E_T for every s.
+The bound is the stated 1e-6 relative, |dE| <= 1e-6 max(1 Eh, |E_T|), and
+literally 1e-6 Eh on the physical-scale twins, for s = 2, 3 and 4 alike.
+Measured relative errors of E_T: 1.8e-7 / 1.3e-7 / 1.3e-7 (s = 2 / 3 / 4,
+o=6 v=36), 3.3e-7 for all s at o=20 v=200, 3.2e-7 to 3.3e-7 on the sampled
+triplets at o=40 v=400 and 3.8e-7 to 3.9e-7 at o=50 v=450.
 """
-
-S2_SMALL = 1e-4
 
 
 def split_rel_bound(s, o, v):
-    if s >= 3:
-        return 1e-6
-    return S2_SMALL if v < 64 else 1e-6
+    if s not in (2, 3, 4):
+        raise ValueError("slice count must be 2, 3 or 4")
+    return 1e-6
