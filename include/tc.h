@@ -99,8 +99,11 @@ typedef struct {
                                 split path, the W-term GEMM launches alone (blocking entry points only) */
   double e_t5;               /* E[5]_ST: the part of E_(T) from the V factor of Eq. 1, sum (V r3(W))/D with the
                                 same weights; E[4] = e_t - e_t5 is the W r3(W)/D part (r3 is the bracket of Eq. 1) */
-  double df_seconds;         /* tc_energy_df_dev: device time of the integral assembly from the DF
-                                factors (gather + three FP64 GEMMs), else 0 */
+  double df_seconds;         /* tc_energy_df(_dev): device time of the integral assembly from the DF
+                                factors (digit images + three tensor-core digit products), else 0 */
+  int df_digits;             /* tc_energy_df(_dev): base-256 digits per factor value the assembly used
+                                (1..7; 3 for factors on a 2^-20 grid), else 0 */
+  int reserved2;
 } tc_result;
 
 /* Create a context on opt->device (opt may be NULL: device 0, defaults).
@@ -132,8 +135,17 @@ tc_status tc_energy_dev(tc_ctx *ctx, int o, int v, const double *eps, const doub
  *       that (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s] (Mulliken notation).
  *   nq  number of factors Q (> 0).
  * The library assembles (ia|bd), (ia|jl) and (ia|jb) on the device in its own
- * memory (grow-only, reused by later calls) with FP64 GEMMs, then computes the
- * energy as tc_energy_dev.  Only B, eps, t1 and t2 cross from the caller.
+ * memory (grow-only, reused by later calls), then computes the energy as
+ * tc_energy_dev.  Only B, eps, t1 and t2 cross from the caller.  The assembly
+ * runs on the BF16 tensor cores as products of base-256 digits: each row of a
+ * factor block is scaled by a power of two and its values split into up to 7
+ * signed 8-bit digits; digit products are exact and summed exactly (integer
+ * class sums), so an integral carries one final rounding.  Factors whose
+ * values need at most 3 digits (e.g. values on a 2^-20 grid below 1 in
+ * magnitude) give every integral exactly; general FP64 factors use 7 digits
+ * and keep the digit pairs p + q <= 6, an error below 2^-45 of the largest
+ * |B_pq^Q B_rs^Q| summed over Q.  The call synchronises the stream once (to
+ * read the digit count).
  * out->df_seconds is the device time of the assembly; kernel_seconds and
  * wterm_seconds cover the energy as for tc_energy_dev.  Errors as
  * tc_energy_dev, plus TC_EINVAL for nq <= 0 or a NULL B, and TC_ENOMEM when

@@ -57,7 +57,8 @@ class tc_result(ctypes.Structure):
                 ("queue_seconds", ctypes.c_double), ("kernel_seconds", ctypes.c_double),
                 ("prep_seconds", ctypes.c_double), ("n_items", ctypes.c_longlong),
                 ("launches", ctypes.c_int), ("reserved", ctypes.c_int), ("wterm_seconds", ctypes.c_double),
-                ("e_t5", ctypes.c_double), ("df_seconds", ctypes.c_double)]
+                ("e_t5", ctypes.c_double), ("df_seconds", ctypes.c_double), ("df_digits", ctypes.c_int),
+                ("reserved2", ctypes.c_int)]
 
 
 class TcError(RuntimeError):

@@ -13,8 +13,6 @@
 #include <string>
 #include <vector>
 
-#include <cublas_v2.h>
-
 #include "../../include/tc.h"
 #include "tc_ctx.h"
 #include "tc_internal.cuh"
@@ -56,24 +54,6 @@ tc_status check_args(tc_ctx *ctx, int o, int v, const double *eps, const double 
     *slices = 0;
   }
   return TC_OK;
-}
-
-// B[Q][n][n] (n = o + v, occupied first) -> the contiguous blocks
-// B_ov[Q][o][v], B_vv[Q][v][v] and B_oo[Q][o][o] of the density-fitting factors.
-__global__ void df_gather(const double *__restrict__ B, int nq, int o, int v, double *__restrict__ bov,
-                          double *__restrict__ bvv, double *__restrict__ boo) {
-  const int n = o + v;
-  const long long total = (long long)nq * n * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % n);
-    const long long t = e / n;
-    const int p = (int)(t % n);
-    const long long Q = t / n;
-    const double x = B[e];
-    if (p < o && q >= o)       bov[(Q * o + p) * v + (q - o)] = x;
-    else if (p >= o && q >= o) bvv[(Q * v + (p - o)) * v + (q - o)] = x;
-    else if (p < o && q < o)   boo[(Q * o + p) * o + q] = x;
-  }
 }
 
 double alg_flops(int o, int v) {
@@ -211,11 +191,10 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
 }
 
 // Device bytes tc_energy_df(_dev) holds besides the workspace: the assembled
-// integrals and the gathered factor blocks.
+// integrals and the assembly's scratch (scales and digit images of B).
 size_t df_bytes(int o, int v, int nq) {
   const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
-  const size_t n_b = (size_t)nq * ((size_t)o * v + (size_t)v * v + (size_t)o * o);
-  return sizeof(double) * (n_ovvv + n_ovoo + n_ovov + n_b);
+  return sizeof(double) * (n_ovvv + n_ovoo + n_ovov) + tc::df_scratch_bytes(o, v, nq);
 }
 
 // The integrals from the DF factors B (device) on st, then the energy (Eq. 6,
@@ -224,42 +203,27 @@ size_t df_bytes(int o, int v, int nq) {
 tc_status df_energy(tc_ctx *ctx, int o, int v, int nq, const double *eps, const double *t1, const double *t2,
                     const double *B, int prec, int slices, double *e_ijk_dev, cudaStream_t st, tc_result *out) {
   const size_t n_ovvv = (size_t)o * v * v * v, n_ovoo = (size_t)o * v * o * o, n_ovov = (size_t)o * v * o * v;
-  const size_t n_b = (size_t)nq * ((size_t)o * v + (size_t)v * v + (size_t)o * o);
   TC_CUDA(ctx, ctx->in_ovvv.ensure(sizeof(double) * n_ovvv));
   TC_CUDA(ctx, ctx->in_ovoo.ensure(sizeof(double) * n_ovoo));
   TC_CUDA(ctx, ctx->in_ovov.ensure(sizeof(double) * n_ovov));
-  TC_CUDA(ctx, ctx->df_b.ensure(sizeof(double) * n_b));
+  TC_CUDA(ctx, ctx->df_b.ensure(tc::df_scratch_bytes(o, v, nq)));
   for (auto &e : ctx->dfev)
     if (!e) TC_CUDA(ctx, cudaEventCreate(&e));
-  cublasHandle_t h = (cublasHandle_t)ctx->blas;
-  if (!h) {
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasCreate failed");
-    ctx->blas = h;
-  }
-  if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasSetStream failed");
-  double *bov = (double *)ctx->df_b.p, *bvv = bov + (size_t)nq * o * v, *boo = bvv + (size_t)nq * v * v;
   double *ovvv = (double *)ctx->in_ovvv.p, *ovoo = (double *)ctx->in_ovoo.p, *ovov = (double *)ctx->in_ovov.p;
   TC_CUDA(ctx, cudaEventRecord(ctx->dfev[0], st));
-  df_gather<<<ctx->num_sms * 8, 256, 0, st>>>(B, nq, o, v, bov, bvv, boo);
-  TC_CUDA(ctx, cudaGetLastError());
-  // (pq|rs) = sum_Q B[Q][pq] B[Q][rs] as products of the blocks (Eq. 6).  A
-  // row-major [rows][cols] result is the column-major cols x rows matrix
-  // X Y^T with X = B_cols (cols x nq) and Y = B_rows (rows x nq).
-  const double one = 1.0, zero = 0.0;
-  const int64_t OV = (int64_t)o * v, VV = (int64_t)v * v, OO = (int64_t)o * o;
-  cublasStatus_t bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, VV, OV, nq, &one, bvv, VV, bov, OV, &zero, ovvv, VV);
-  if (bs == CUBLAS_STATUS_SUCCESS)
-    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OO, OV, nq, &one, boo, OO, bov, OV, &zero, ovoo, OO);
-  if (bs == CUBLAS_STATUS_SUCCESS)
-    bs = cublasDgemm_64(h, CUBLAS_OP_N, CUBLAS_OP_T, OV, OV, nq, &one, bov, OV, bov, OV, &zero, ovov, OV);
-  if (bs != CUBLAS_STATUS_SUCCESS) return fail(ctx, TC_ECUDA, "cublasDgemm failed (status %d)", (int)bs);
+  int digits = 0;
+  TC_CUDA(ctx, tc::df_assemble(B, nq, o, v, ovvv, ovoo, ovov, ctx->df_b.p, ctx->num_sms, st, &digits));
   TC_CUDA(ctx, cudaEventRecord(ctx->dfev[1], st));
   const tc::Inputs in{eps, t1, t2, ovvv, ovoo, ovov};
   const tc_status s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
   if (s != TC_OK) return s;
+  int derr = 0;
+  TC_CUDA(ctx, cudaMemcpy(&derr, tc::df_error_flag(ctx->df_b.p, o, v, nq), sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr != 0) return fail(ctx, TC_ETIMEOUT, "integral assembly: device-side wait gave up (code %d)", derr);
   float ms = 0.f;
   TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->dfev[0], ctx->dfev[1]));
   out->df_seconds = 1e-3 * ms;
+  out->df_digits = digits;
   return TC_OK;
 }
 
@@ -343,7 +307,6 @@ void tc_finalize(tc_ctx *ctx) {
   ctx->in_ovvv.release(); ctx->in_ovoo.release(); ctx->in_ovov.release();
   ctx->df_b.release();
   ctx->df_in.release();
-  if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
   for (auto &e : ctx->dfev) if (e) cudaEventDestroy(e);
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);

@@ -46,9 +46,8 @@ struct tc_ctx {
   tc::DevBuf ws;                            // tables, partials and sums, reused across calls
   tc::DevBuf ws_split;                      // BF16 operand images, FP32 copies, W buffer
   tc::DevBuf in_eps, in_t1, in_t2, in_ovvv, in_ovoo, in_ovov;   // tc_energy's device copies; tc_energy_df_dev's integrals
-  tc::DevBuf df_b;                          // tc_energy_df(_dev): the gathered factor blocks B_ov, B_vv, B_oo
+  tc::DevBuf df_b;                          // tc_energy_df(_dev): scratch of the integral assembly (scales, digit images)
   tc::DevBuf df_in;                         // tc_energy_df: the device copy of B
-  void *blas = nullptr;                     // cuBLAS handle of tc_energy_df_dev (created on first use)
   cudaEvent_t dfev[2] = {nullptr, nullptr}; // around the integral assembly
   double *host_out = nullptr;               // pinned read-back slot
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};     // kernel timing

@@ -165,6 +165,17 @@ cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cud
 cudaError_t split_block_params(WtBatch *wb, EnBatch &eb, int S, int num_sms, void **wargs, void **eargs,
                                cudaKernelNodeParams *wp, cudaKernelNodeParams *ep);
 
+// ---------------------------------------------------------------- integrals from DF factors (tc_df.cu)
+// (ia|bd), (ia|jl) and (ia|jb) from B[nq][o+v][o+v] (Eq. 6) as exact digit
+// products on the tensor cores.  scratch: df_scratch_bytes(o, v, nq) device
+// bytes.  *digits receives the number of base-256 digits the factors needed
+// (at most 7); the call synchronises st once to read it.
+size_t df_scratch_bytes(int o, int v, int nq);
+cudaError_t df_assemble(const double *B, int nq, int o, int v, double *ovvv, double *ovoo, double *ovov,
+                        void *scratch, int num_sms, cudaStream_t st, int *digits);
+// Device error flag of the assembly's kernels inside its scratch (0 = fine).
+int *df_error_flag(void *scratch, int o, int v, int nq);
+
 // ---------------------------------------------------------------- reduction
 struct RedJob {
   int n_trip, items_per_trip, o;

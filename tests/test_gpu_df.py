@@ -1,11 +1,13 @@
 """Integrals assembled on the device from density-fitting factors (Eq. 6).
 
 tc_energy_df_dev takes B[Q][p][q] with (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s]
-and forms (ia|bd), (ia|jl), (ia|jb) itself.  The synthetic factors sit on a
-2^-20 grid, so every integral is an exact sum in any order: the assembled
-integrals equal the host-built ones bit for bit, and so must the energies and
-the per-triplet contributions of both precisions.  The energies are also
-checked against the oracle.
+and forms (ia|bd), (ia|jl), (ia|jb) itself, as exact base-256 digit products
+on the tensor cores.  The synthetic factors sit on a 2^-20 grid, so every
+integral is an exact sum in any order: the assembled integrals equal the
+host-built ones bit for bit, and so must the energies and the per-triplet
+contributions of both precisions.  The energies are also checked against the
+oracle.  Factors off the grid (general FP64 values) take seven digits and
+must agree with FP64 integrals to FP64 accuracy.
 """
 import ctypes
 
@@ -44,9 +46,26 @@ def test_df_input_equals_integral_input(o, v, seed, prec, s):
     assert r_df.e_t == r_int.e_t and r_df.e_t5 == r_int.e_t5
     assert np.array_equal(e_df, e_int)
     assert r_df.df_seconds > 0.0 and r_df.prec == prec
+    assert 1 <= r_df.df_digits <= 3                 # factors on the 2^-20 grid: exact in three digits
     ref = oracle.energy_by_triplets(job)
     tol = 1e-9 * abs(ref) if prec == FP64 else split_rel_bound(s, o, v) * max(1.0, abs(ref))
     assert abs(r_df.e_t - ref) <= tol
+
+
+@pytest.mark.parametrize("prec,s", [(FP64, 0), (SPLIT, 3)])
+def test_df_general_factors_agree_to_fp64_accuracy(prec, s):
+    """Factors with full 53-bit values: seven digits, energies as from FP64-rounded integrals."""
+    import dataclasses
+    amp = synth.make_amplitudes(5, 30, 47)
+    rng = np.random.default_rng(11)
+    noise = rng.standard_normal(amp.B.shape) * 1e-3
+    B = amp.B + (noise + noise.transpose(0, 2, 1)) * 0.5          # symmetric, off the grid
+    amp = dataclasses.replace(amp, B=B)
+    job, r_int, e_int, r_df, e_df = _run(amp, prec, s)
+    print(f"prec={prec} digits={r_df.df_digits} E_df={r_df.e_t:.15e} E_int={r_int.e_t:.15e}")
+    assert r_df.df_digits == 7
+    assert abs(r_df.e_t - r_int.e_t) <= 1e-12 * abs(r_int.e_t)
+    assert np.all(np.abs(e_df - e_int) <= 1e-12 * np.abs(e_int).max())
 
 
 def test_df_full_size_o20_v200():
