@@ -122,11 +122,11 @@ class ClockSampler:
 def kernel_source_hash(prec):
     """Hash of the kernel source with comments and blank lines removed (a comment edit keeps it)."""
     import re
-    name = "tc_fp64.cu" if prec == "fp64" else "tc_split.cu"
-    p = os.path.join(ROOT, "paper_2512_01055_gb300", "csrc", name)
-    if not os.path.exists(p):
+    names = ["tc_fp64.cu"] if prec == "fp64" else ["tc_split.cu", "tc_ptx.cuh"]
+    paths = [os.path.join(ROOT, "paper_2512_01055_gb300", "csrc", n) for n in names]
+    if not all(os.path.exists(p) for p in paths):
         return None
-    src = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+    src = re.sub(r"/\*.*?\*/", "", "".join(open(p).read() for p in paths), flags=re.S)
     src = "\n".join(line.split("//")[0].rstrip() for line in src.splitlines())
     src = "\n".join(line for line in src.splitlines() if line.strip())
     return hashlib.sha256(src.encode()).hexdigest()[:16]
@@ -509,6 +509,16 @@ def main():
     te = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, device)
     del host
 
+    # the same energy from the DF factor (tc_energy_df_dev: the integral blocks
+    # assembled on the device as exact digit products on the tensor cores)
+    Bdev = torch.from_numpy(np.ascontiguousarray(amp.B)).to(device)
+    rdf = tc.tc_energy_df_dev(ctx, o, v, Bdev, dev["eps"], dev["t1"], dev["t2"], prec=head_prec, slices=head_slices,
+                              stream=stream)
+    df_line = {"entry": "tc_energy_df_dev", "df_seconds": rdf.df_seconds, "digits": rdf.df_digits,
+               "kernel_seconds": rdf.kernel_seconds, "df_over_kernel": rdf.df_seconds / rdf.kernel_seconds,
+               "s_per_energy": rdf.seconds, "same_e_t": rdf.e_t == head["e_t"]}
+    del Bdev
+
     fp64 = None
     if head_prec != tc.TC_FP64 and (args.fp64_full or flops < 5e13):
         fp64 = timed(tc.TC_FP64, 0, 1, 1, False)
@@ -555,6 +565,7 @@ def main():
                          "traffic": recorded_traffic(kname, name, "fp64" if pairs == 1 else "split"),
                          "kernel": kname, "kernel_ms": 1e3 * head["wterm"], "peak_source": peak_note},
         }
+        out["df"] = df_line
         if per_slices:
             out["slices"] = per_slices
         if sampled:
