@@ -31,7 +31,9 @@
 // every KCHAIN blocks (256 K values): the drain warps (a thread holds one tile
 // row, half its columns) add each finished chain into the row's FP32 sum in
 // registers; on the last chain they add L1 and write the row, in [a][b][c]
-// orientation, into the job's W buffer Y[triplet][a][b][c].  The three F
+// orientation, into the job's W buffer Y[triplet][a][b][c].  While the drain
+// reads a finished chain's L0, the MMA warp issues the L1 products of the next
+// chain's first DEFER K blocks and only then their level-0 products.  The three F
 // launches of a block run in order: the first stores, the other two add their
 // rows to the stored values (L2 reductions), so Y ends as W with each
 // element's three contributions added in one fixed order.  Shared memory holds only the
@@ -84,6 +86,9 @@ constexpr int MAXG = (NCMAX / 16 + 1) / 2;   // 16-column groups a drain thread 
 constexpr int SMEM_DYN_MAX = 232448 - 2048;  // opt-in limit minus static shared memory and slack
 // Longest run of K blocks accumulated in one tensor-core accumulator (see above).
 constexpr int KCHAIN = 16;
+// K blocks of a later chain whose level-0 products wait for the drain to free
+// L0 while their higher-level products already run (fewer than the stages).
+constexpr int DEFER = 4;
 
 constexpr int ERR_TIMEOUT_FULL = 11, ERR_TIMEOUT_EMPTY = 12, ERR_TIMEOUT_ACCFULL = 13,
               ERR_TIMEOUT_ACCEMPTY = 14, ERR_TIMEOUT_TEARDOWN = 15;
@@ -309,13 +314,17 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         const uint32_t ahb = (uint32_t)S * A_HALF, bhb = (uint32_t)S * nc * 16;
         for (int ch = 0; ok && ch < nchain; ++ch) {
           const int kc0 = ch * nkb / nchain, kc1 = (ch + 1) * nkb / nchain;
-          // A new item needs both accumulators back from the drain; a later
-          // chain needs only L0, so its first K block issues the L1 MMAs first
-          // and waits for L0 only before its level-0 MMA.
+          // A new item needs both accumulators back from the drain.  A later
+          // chain needs only L0, which the drain is still reading: its first
+          // ndef K blocks issue their L1 products first, and their level-0
+          // products (in K order, the first one restarting L0) follow once L0
+          // is free, so the tensor pipe keeps working meanwhile.
           if (ch == 0) {
             if (!mbar_wait(&accempty_bar, aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           }
+          const int ndef = ch > 0 ? min(DEFER, kc1 - kc0) : 0;
+          int dstage[DEFER];
           for (int kc = kc0; kc < kc1; ++kc) {
             if (!mbar_wait(&full_bar[stage], phase, &abort_flag, B.err, ERR_TIMEOUT_FULL)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -331,9 +340,18 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
                          (kc == 0 && n == 0) ? 0u : 1u);
                 ++n;
               }
-            if (kc == kc0 && ch > 0) {
+            if (kc - kc0 < ndef) {
+              dstage[kc - kc0] = stage;                                            // level 0 deferred
+              if (++stage == B.stages) { stage = 0; phase ^= 1u; }
+              if (kc - kc0 + 1 < ndef) continue;
               if (!mbar_wait(&accempty_bar, aphase ^ 1u, &abort_flag, B.err, ERR_TIMEOUT_ACCEMPTY)) { ok = false; break; }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              for (int d = 0; d < ndef; ++d) {
+                const uint32_t dA = smem_u32(sm + (size_t)dstage[d] * B.slot), dB = dA + 2 * ahb;
+                mma_bf16(tbase, sdesc(dA, ahb), sdesc(dB, bhb), id, d > 0 ? 1u : 0u);   // level 0 -> L0
+                mma_commit(&empty_bar[dstage[d]]);
+              }
+              continue;
             }
             mma_bf16(tbase, sdesc(sA, ahb), sdesc(sB, bhb), id, kc > kc0 ? 1u : 0u);  // level 0 -> L0
             mma_commit(&empty_bar[stage]);
@@ -1058,7 +1076,7 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
   }
   wb.total_items = total;
   const WtShape sh = wt_shape(S, ncmax);
-  if (sh.stages < 2) return cudaErrorInvalidValue;
+  if (sh.stages <= DEFER) return cudaErrorInvalidValue;     // deferred K blocks hold stages
   wb.stages = sh.stages;
   wb.nprod = sh.nprod;
   wb.slot = sh.slot;
