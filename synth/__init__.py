@@ -236,6 +236,107 @@ def serving_request_shape(r: int) -> tuple[int, int]:
 
 
 # ---------------------------------------------------------------------------
+# The same generator on a CUDA device (serving streams of hundreds of jobs,
+# where drawing hundreds of millions of numbers on the host would dominate).
+# SplitMix64 runs in 64-bit integer arithmetic (wrapping multiplications,
+# logical shifts built from arithmetic ones), so the raw draws and the
+# uniforms are bit-identical to the host generator's; the Box-Muller normals
+# use the device's log and cos and may differ from the host's in the last
+# place, and so may (rarely) a factor value rounded to the 2^-20 grid.
+# ---------------------------------------------------------------------------
+
+def _to_i64(x: int) -> int:
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _srl(z, k: int):
+    """Logical right shift of int64 tensors."""
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(z, k), (1 << (64 - k)) - 1)
+
+
+def _mix_t(z):
+    """The SplitMix64 finaliser on int64 tensors (multiplications wrap modulo 2^64)."""
+    import torch
+    z = torch.bitwise_xor(z, _srl(z, 30)) * _to_i64(int(_M1))
+    z = torch.bitwise_xor(z, _srl(z, 27)) * _to_i64(int(_M2))
+    return torch.bitwise_xor(z, _srl(z, 31))
+
+
+def uniform_t(seed: int, tag: int, start: int, count: int, device):
+    """Device twin of uniform(): 53-bit uniforms in [0, 1), float64 tensor."""
+    import torch
+    s0 = _to_i64(int(stream_seed(seed, tag)))
+    n = torch.arange(start + 1, start + 1 + count, dtype=torch.int64, device=device)
+    z = _mix_t(s0 + n * _to_i64(int(_GOLDEN)))
+    return _srl(z, 11).to(torch.float64) * 2.0 ** -53
+
+
+def normal_t(seed: int, tag: int, start: int, count: int, device):
+    """Device twin of normal() (uniforms 2n and 2n+1, Box-Muller cosine branch)."""
+    import torch
+    u = uniform_t(seed, tag, 2 * start, 2 * count, device)
+    u1 = 1.0 - u[0::2]
+    u2 = u[1::2]
+    return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * torch.pi * u2)
+
+
+def make_amplitudes_device(o: int, v: int, seed: int, device="cuda", Q: int | None = None):
+    """make_amplitudes() drawn on a CUDA device: dict of float64 tensors eps, B, t1, t2."""
+    import torch
+    N = o + v
+    if Q is None:
+        Q = 3 * N
+    eps_o = torch.sort(-1.5 + 1.2 * uniform_t(seed, TAG_EPS_OCC, 0, o, device)).values
+    eps_v = torch.sort(0.1 + 2.9 * uniform_t(seed, TAG_EPS_VIR, 0, v, device)).values
+    iu, ju = torch.triu_indices(N, N, device=device)
+    npair = iu.numel()
+    B = torch.empty((Q, N, N), dtype=torch.float64, device=device)
+    step = max(1, (1 << 25) // max(npair, 1))
+    for q0 in range(0, Q, step):
+        q1 = min(Q, q0 + step)
+        x = normal_t(seed, TAG_B, q0 * npair, (q1 - q0) * npair, device).reshape(q1 - q0, npair) * B_SIGMA
+        x = torch.clamp(torch.round(x / B_GRID) * B_GRID, -B_CLIP, B_CLIP)
+        B[q0:q1, iu, ju] = x
+        B[q0:q1, ju, iu] = x
+    t1 = (normal_t(seed, TAG_T1, 0, o * v, device) * T1_SIGMA).reshape(o, v)
+    ov = o * v
+    # upper triangle (I <= J) of the (i a) x (j b) matrix in row-major order of the triangle
+    t2m = torch.empty((ov, ov), dtype=torch.float64, device=device)
+    I, J = torch.triu_indices(ov, ov, device=device)
+    base = I * ov - I * (I - 1) // 2                       # draws before row I
+    idx = base + (J - I)
+    total = ov * (ov + 1) // 2
+    chunk = 1 << 25
+    for c0 in range(0, total, chunk):
+        c1 = min(total, c0 + chunk)
+        x = normal_t(seed, TAG_T2, c0, c1 - c0, device) * T2_SIGMA
+        sel = slice(c0, c1)                                # idx is increasing: positions c0..c1 of the triangle
+        t2m[I[sel], J[sel]] = x
+        t2m[J[sel], I[sel]] = x
+    del I, J, base, idx
+    t2 = t2m.reshape(o, v, o, v).permute(0, 2, 1, 3).contiguous()
+    return {"o": o, "v": v, "eps": torch.cat([eps_o, eps_v]), "B": B, "t1": t1.contiguous(), "t2": t2}
+
+
+def device_job_from_factor(amp: dict):
+    """Integral blocks from a device-drawn job (make_amplitudes_device): dict as device_job()."""
+    import torch
+    o, v, B = amp["o"], amp["v"], amp["B"]
+    Q = B.shape[0]
+    Bov = B[:, :o, o:].reshape(Q, o * v)
+    Bvv = B[:, o:, o:].reshape(Q, v * v)
+    Boo = B[:, :o, :o].reshape(Q, o * o)
+    ovvv = torch.empty((o, v, v, v), dtype=torch.float64, device=B.device)
+    for i in range(o):
+        ovvv[i] = (Bov.reshape(Q, o, v)[:, i, :].T @ Bvv).reshape(v, v, v)
+    return dict(eps=amp["eps"], t1=amp["t1"], t2=amp["t2"], ovvv=ovvv,
+                ovoo=(Bov.T @ Boo).reshape(o, v, o, o).contiguous(),
+                ovov=(Bov.T @ Bov).reshape(o, v, o, v).contiguous())
+
+
+# ---------------------------------------------------------------------------
 # Device copies of a job (large workloads): the integral blocks are formed on
 # the GPU with FP64 matrix products of the same DF factor.  Because every B
 # value sits on a 2^-20 grid, each product sum is exact, so the device blocks

@@ -51,3 +51,21 @@ def test_serving_shapes_in_range():
     for r in range(200):
         o, v = synth.serving_request_shape(r)
         assert 6 <= o <= 32 and 6 * o - 1 <= v <= 12 * o + 1
+
+
+def test_device_generator_twin_matches_host_generator():
+    """The torch twin (run here on the CPU) draws the same uniforms bit for bit;
+    normals agree to the last place (log/cos of another math library), and the
+    factor values, rounded to the 2^-20 grid, agree exactly on these shapes."""
+    import torch
+    for (o, v, seed) in [(3, 7, 5), (4, 11, synth.SERVING_SEED_BASE + 7)]:
+        assert np.array_equal(synth.uniform(seed, 5, 3, 200), synth.uniform_t(seed, 5, 3, 200, "cpu").numpy())
+        a = synth.make_amplitudes(o, v, seed)
+        b = synth.make_amplitudes_device(o, v, seed, device="cpu")
+        assert np.array_equal(a.eps, b["eps"].numpy())
+        assert np.array_equal(a.B, b["B"].numpy())
+        assert np.allclose(a.t1, b["t1"].numpy(), rtol=1e-14, atol=0)
+        assert np.allclose(a.t2, b["t2"].numpy(), rtol=1e-13, atol=1e-20)
+        d = synth.device_job_from_factor(b)
+        assert np.array_equal(d["ovoo"].numpy(), synth.ovoo(a))
+        assert torch.equal(d["ovov"], torch.from_numpy(synth.ovov(a)))
