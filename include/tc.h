@@ -239,6 +239,11 @@ typedef struct {
   int slices;                    /* TC_SPLIT_BF16: 2..4, <= 0 for the default */
   int flags;                     /* 0: host arrays, copied before tc_submit returns;
                                     TC_JOB_DEVICE_INPUTS: resident device arrays, not copied */
+  int nq;                        /* > 0: the integrals come from the density-fitting factors B
+                                    (Eq. 6) and ints is ignored (may hold NULLs); 0: from ints */
+  const double *B;               /* nq > 0: [nq][o+v][o+v] as for tc_energy_df, host or device per
+                                    flags; the service assembles the integrals on the device when it
+                                    admits the job (in the job's own memory, counted in its footprint) */
 } tc_job;
 
 /* Queue a job.  *ticket identifies it in tc_poll / tc_wait / tc_cancel.

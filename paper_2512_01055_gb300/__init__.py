@@ -42,7 +42,7 @@ class tc_ints(ctypes.Structure):
 class tc_job(ctypes.Structure):
     _fields_ = [("o", ctypes.c_int), ("v", ctypes.c_int), ("eps", ctypes.c_void_p), ("t1", ctypes.c_void_p),
                 ("t2", ctypes.c_void_p), ("ints", tc_ints), ("prec", ctypes.c_int), ("slices", ctypes.c_int),
-                ("flags", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("nq", ctypes.c_int), ("B", ctypes.c_void_p)]
 
 
 class tc_serve_stats(ctypes.Structure):
@@ -330,11 +330,18 @@ def tc_combine_parts(parts):
 # Serving
 # ---------------------------------------------------------------------------
 
-def tc_submit(ctx, o, v, eps, t1, t2, ovvv, ovoo, ovov, prec=TC_FP64, slices=0, device_inputs=False) -> int:
-    """Queue one job; host numpy arrays are copied before return, device tensors stay resident (caller keeps them)."""
+def tc_submit(ctx, o, v, eps, t1, t2, ovvv=None, ovoo=None, ovov=None, prec=TC_FP64, slices=0, device_inputs=False,
+              B=None) -> int:
+    """Queue one job; host numpy arrays are copied before return, device tensors stay resident (caller keeps them).
+
+    With B ([nq, o+v, o+v] density-fitting factors) the service assembles the
+    integrals itself when it admits the job, and ovvv / ovoo / ovov are not given.
+    """
     ptr = _ptr_dev if device_inputs else _ptr_np
-    job = tc_job(o, v, ptr(eps), ptr(t1), ptr(t2), tc_ints(ptr(ovvv), ptr(ovoo), ptr(ovov)), prec, slices,
-                 TC_JOB_DEVICE_INPUTS if device_inputs else 0)
+    nq = 0 if B is None else int(B.shape[0])
+    ints = tc_ints(None, None, None) if B is not None else tc_ints(ptr(ovvv), ptr(ovoo), ptr(ovov))
+    job = tc_job(o, v, ptr(eps), ptr(t1), ptr(t2), ints, prec, slices,
+                 TC_JOB_DEVICE_INPUTS if device_inputs else 0, nq, ptr(B) if B is not None else None)
     ticket = ctypes.c_uint64()
     s = load().tc_submit(ctx, ctypes.byref(job), ctypes.byref(ticket))
     if s != TC_OK:

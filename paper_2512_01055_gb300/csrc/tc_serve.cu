@@ -43,10 +43,13 @@ struct Req {
   uint64_t id = 0;
   int o = 0, v = 0, prec = 0, slices = 0, group = 0;
   bool dev_inputs = false;
-  std::vector<double> host[6];            // copies of host inputs (eps, t1, t2, ovvv, ovoo, ovov)
+  int nq = 0;                             // > 0: integrals from the DF factors (Eq. 6)
+  std::vector<double> host[6];            // copies of host inputs (eps, t1, t2, ovvv, ovoo, ovov; B in [3] for DF)
   const double *din[6] = {};              // device inputs used by the kernels
-  char *mem = nullptr;                    // device block: [inputs][workspace][split images]
+  const double *dB = nullptr;             // DF factors on the device
+  char *mem = nullptr;                    // device block: [host inputs][DF integrals][DF scratch][workspace][split images]
   size_t footprint = 0;
+  size_t off_ints = 0, off_df = 0;        // DF jobs: assembled integrals and assembly scratch in the block
   Dims d{};
   plan::Layout L{};
   SplitLayout SL{};
@@ -150,7 +153,6 @@ void Server::fail_job(const std::shared_ptr<Req> &r, tc_status s) {
 void Server::start_prep(const std::shared_ptr<Req> &r) {
   Req &q = *r;
   const bool split = q.prec == TC_SPLIT_BF16;
-  const size_t in_b = q.dev_inputs ? 0 : plan::align256(plan::input_bytes(q.o, q.v));
   cudaError_t e = cudaSuccess;
   if (q.inject_alloc_fault) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = cudaMallocAsync((void **)&q.mem, q.footprint, q.st);
@@ -167,16 +169,41 @@ void Server::start_prep(const std::shared_ptr<Req> &r) {
   if (!q.dev_inputs) {
     const size_t O = q.o, V = q.v;
     const size_t n[6] = {O + V, O * V, O * O * V * V, O * V * V * V, O * V * O * O, O * V * O * V};
+    const int narr = q.nq > 0 ? 4 : 6;    // DF: eps, t1, t2, B
     size_t off = 0;
-    for (int a = 0; a < 6; ++a) {
+    for (int a = 0; a < narr; ++a) {
       double *dst = (double *)(q.mem + off);
-      cudaMemcpyAsync(dst, q.host[a].data(), n[a] * sizeof(double), cudaMemcpyHostToDevice, q.st);
-      q.din[a] = dst;
-      off += n[a] * sizeof(double);
+      const size_t cnt = (q.nq > 0 && a == 3) ? q.host[3].size() : n[a];
+      cudaMemcpyAsync(dst, q.host[a].data(), cnt * sizeof(double), cudaMemcpyHostToDevice, q.st);
+      if (q.nq > 0 && a == 3) q.dB = dst;
+      else q.din[a] = dst;
+      off += cnt * sizeof(double);
     }
   }
-  q.off_ws = in_b;
-  q.off_split = in_b + q.L.total;
+  if (q.nq > 0) {
+    // the integral blocks from the factors, in the job's block (Eq. 6)
+    const size_t O = q.o, V = q.v;
+    double *ovvv = (double *)(q.mem + q.off_ints), *ovoo = ovvv + O * V * V * V, *ovov = ovoo + O * V * O * O;
+    int digits = 0;
+    e = df_assemble(q.dB, q.nq, q.o, q.v, ovvv, ovoo, ovov, q.mem + q.off_df, ctx->num_sms, q.st, &digits);
+    q.din[3] = ovvv;
+    q.din[4] = ovoo;
+    q.din[5] = ovov;
+    q.res.df_digits = digits;
+    if (e == cudaSuccess) {
+      int derr = 0;
+      e = cudaMemcpyAsync(&derr, df_error_flag(q.mem + q.off_df, q.o, q.v, q.nq), sizeof(int), cudaMemcpyDeviceToHost,
+                          q.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(q.st);
+      if (e == cudaSuccess && derr != 0) e = cudaErrorLaunchTimeout;
+    }
+    if (e != cudaSuccess) {
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto &h : q.host) std::vector<double>().swap(h);
+      fail_job(r, e == cudaErrorLaunchTimeout ? TC_ETIMEOUT : TC_ECUDA);
+      return;                             // memory released by the scheduler's sweep
+    }
+  }
   char *base = q.mem + q.off_ws;
   const std::vector<int4> tab = plan::tables(q.d, q.L, nullptr);
   cudaMemcpyAsync(base + q.L.trip, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, q.st);
@@ -504,7 +531,8 @@ tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket) {
   int prec = job->prec < 0 ? ctx->default_prec : job->prec;
   int slices = job->slices <= 0 ? ctx->default_slices : job->slices;
   if (o <= 0 || v <= 0 || (long long)o * v * v * v > (1LL << 40)) return TC_EINVAL;
-  if (!job->eps || !job->t1 || !job->t2 || !job->ints.ovvv || !job->ints.ovoo || !job->ints.ovov) return TC_EINVAL;
+  if (job->nq < 0 || !job->eps || !job->t1 || !job->t2) return TC_EINVAL;
+  if (job->nq > 0 ? !job->B : (!job->ints.ovvv || !job->ints.ovoo || !job->ints.ovov)) return TC_EINVAL;
   if (prec != TC_FP64 && prec != TC_SPLIT_BF16) return TC_EINVAL;
   if (prec == TC_SPLIT_BF16 && (slices < 2 || slices > 4)) return TC_EINVAL;
   if (prec == TC_FP64) slices = 0;
@@ -523,18 +551,31 @@ tc_status tc_submit(tc_ctx *ctx, const tc_job *job, uint64_t *ticket) {
               : tc::plan::make_dims(o, v, tc::fp64_tile());
   r->L = tc::plan::make_layout(r->d);
   if (split) r->SL = tc::split_layout(o, v, slices);
-  r->footprint = (r->dev_inputs ? 0 : tc::plan::align256(tc::plan::input_bytes(o, v))) + r->L.total + r->SL.total;
+  r->nq = job->nq;
+  const size_t O = o, V = v, NB = (size_t)job->nq * (O + V) * (O + V);
+  const size_t ints_b = sizeof(double) * (O * V * V * V + O * V * O * O + O * V * O * V);
+  // [host inputs][DF integrals][DF scratch][workspace][split images]
+  const size_t in_b = r->dev_inputs ? 0
+                      : tc::plan::align256(r->nq > 0 ? sizeof(double) * (O + V + O * V + O * O * V * V + NB)
+                                                     : tc::plan::input_bytes(o, v));
+  r->off_ints = in_b;
+  r->off_df = r->off_ints + (r->nq > 0 ? tc::plan::align256(ints_b) : 0);
+  r->off_ws = r->off_df + (r->nq > 0 ? tc::plan::align256(tc::df_scratch_bytes(o, v, r->nq)) : 0);
+  r->off_split = r->off_ws + r->L.total;
+  r->footprint = r->off_split + r->SL.total;
   // cost units: one orbit's worth of K values; a split unit is a whole triplet
   r->units = split ? r->d.n_trip : r->d.n_items;
   r->cost_per_item = (double)(split ? r->d.n_orb : r->d.orb_per_item) * (v + 16.0 * ((o + 15) / 16));
   if (r->footprint > ctx->budget) return TC_ENOMEM;
   const double *src[6] = {job->eps, job->t1, job->t2, job->ints.ovvv, job->ints.ovoo, job->ints.ovov};
-  const size_t O = o, V = v;
   const size_t n[6] = {O + V, O * V, O * O * V * V, O * V * V * V, O * V * O * O, O * V * O * V};
+  const int narr = r->nq > 0 ? 3 : 6;
   if (r->dev_inputs) {
-    for (int a = 0; a < 6; ++a) r->din[a] = src[a];
+    for (int a = 0; a < narr; ++a) r->din[a] = src[a];
+    if (r->nq > 0) r->dB = job->B;
   } else {
-    for (int a = 0; a < 6; ++a) r->host[a].assign(src[a], src[a] + n[a]);
+    for (int a = 0; a < narr; ++a) r->host[a].assign(src[a], src[a] + n[a]);
+    if (r->nq > 0) r->host[3].assign(job->B, job->B + NB);
   }
   if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess) return TC_ECUDA;
   r->res.o = o;

@@ -165,3 +165,41 @@ def test_invalid_submissions():
         assert tc.tc_poll(ctx, 987654)[0] == tc.TC_EINVAL
     finally:
         tc.tc_finalize(ctx)
+
+
+def test_factor_jobs_assembled_by_the_service_equal_integral_jobs():
+    """Jobs given as DF factors (the service assembles the integrals on admission)
+    give the bits of the same jobs given as integral arrays, host or device
+    inputs, alone and mixed with integral jobs."""
+    import torch
+    specs = [(6, 40, 121, tc.TC_FP64, 0), (8, 50, 122, SPLIT, 3), (5, 33, 123, SPLIT, 2), (7, 44, 124, SPLIT, 3)]
+    amps = [synth.make_amplitudes(o, v, seed) for (o, v, seed, _, _) in specs]
+    jobs = [synth.Job(o=a.o, v=a.v, eps=a.eps, t1=a.t1, t2=a.t2, ovvv=synth.ovvv(a), ovoo=synth.ovoo(a),
+                      ovov=synth.ovov(a)) for a in amps]
+    ref = [alone(j, p, s) for j, (_, _, _, p, s) in zip(jobs, specs)]
+    ctx = tc.tc_init(0, max_inflight=8, iteration_ms=5)
+    f = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+    keep = []                      # device inputs stay valid until their jobs complete
+    try:
+        tickets = []
+        for n, (a, (o, v, _, p, s)) in enumerate(zip(amps, specs)):
+            if n % 2:
+                d = [f(a.eps), f(a.t1), f(a.t2), f(a.B)]
+                keep.append(d)
+                tickets.append(tc.tc_submit(ctx, o, v, d[0], d[1], d[2], prec=p, slices=s,
+                                            device_inputs=True, B=d[3]))
+            else:
+                tickets.append(tc.tc_submit(ctx, o, v, a.eps, a.t1, a.t2, prec=p, slices=s,
+                                            B=np.ascontiguousarray(a.B)))
+            tickets.append(tc.tc_submit(ctx, o, v, jobs[n].eps, jobs[n].t1, jobs[n].t2, jobs[n].ovvv, jobs[n].ovoo,
+                                        jobs[n].ovov, prec=p, slices=s))
+        for n, t in enumerate(tickets):
+            st, res = tc.tc_wait(ctx, t, 120000)
+            assert st == tc.TC_OK, (n, tc.status_str(st))
+            assert res.e_t == ref[n // 2], (n, res.e_t, ref[n // 2])
+            if n % 2 == 0:
+                assert 1 <= res.df_digits <= 3
+        stats = tc.tc_serve_stats_get(ctx)
+        assert stats.failed == 0 and stats.reserved_bytes == 0
+    finally:
+        tc.tc_finalize(ctx)
