@@ -274,7 +274,19 @@ def serving_requests(n, fp64_share, slices):
 
 
 def serving(args):
-    """Continuous-batching service on one GPU: p50/p99 latency and jobs/s at a stated arrival rate."""
+    """Continuous-batching service on one GPU: p50/p99 latency and jobs/s at a stated arrival rate.
+
+    The seeded stream: request r has o ~ U{6..32}, v = round(o U[6,12]),
+    Q = 3 (o + v), its own seed, and arrives at a Poisson time.  A client
+    thread draws each request's inputs on the device (the seeded generator's
+    device twin: orbital energies, amplitudes and the density-fitting factor)
+    shortly before its arrival, with at most --lookahead-gb of drawn but
+    unfinished inputs; at the arrival time the request is submitted with its
+    device arrays and its factor (TC_JOB_DEVICE_INPUTS, nq = Q: the service
+    assembles the integrals on admission), and its arrays are released once it
+    completes.  Latency = completion - the scheduled arrival (so any client
+    delay counts against the service).
+    """
     import threading
     import torch
     import paper_2512_01055_gb300 as tc
@@ -284,63 +296,122 @@ def serving(args):
     torch.cuda.set_device(0)
     tcbuild.build()
     reqs, offs = serving_requests(args.requests, args.fp64_share, args.slices)
-    # service-time estimate from the measured single-job rates (FP64 ~0.9 TF/s, split ~130 TF/s at s=3)
-    est = [alg_flops(o, v) / (0.9e12 if p == 0 else 130e12 * 6.0 / (s * (s + 1) / 2)) for (o, v, _, p, s) in reqs]
+    flops = [alg_flops(o, v) for (o, v, _, _, _) in reqs]
+    # service-time model for the arrival rate: FP64 ~0.9 TF/s; split 130 TF/s at s = 3 (the
+    # service's aggregate rate over the mix of sizes; large jobs alone reach ~200), scaled by the
+    # slice pairs, plus a fixed 30 ms per job (tables, images, reduction)
+    est = [f / (0.9e12 if p == 0 else 130e12 * 6.0 / (s * (s + 1) / 2)) + 0.03
+           for f, (_, _, _, p, s) in zip(flops, reqs)]
     capacity = 1.0 / max(1e-9, float(np.mean(est)))
     rate = args.rate if args.rate > 0 else args.load * capacity
     arrivals = offs / rate
-    t_gen = time.perf_counter()
-    devs = [synth.device_job(synth.make_amplitudes(o, v, seed)) for (o, v, seed, _, _) in reqs]
-    torch.cuda.synchronize()
-    t_gen = time.perf_counter() - t_gen
-    ctx = tc.tc_init(0, max_inflight=16, iteration_ms=50)
-    tickets = [None] * len(reqs)
-    results = [None] * len(reqs)
+    free0, total_mem = torch.cuda.mem_get_info()
+    budget = int(args.budget_frac * free0)
+    ctx = tc.tc_init(0, hbm_budget_bytes=budget, max_inflight=16, iteration_ms=50)
+    n = len(reqs)
+    devs = [None] * n
+    ready = [threading.Event() for _ in range(n)]
+    tickets = [None] * n
+    submit_t = [None] * n
+    results = [None] * n
+    pending_bytes = [0]
+    cv = threading.Condition()
     done = threading.Event()
+    gen_s = [0.0]
+    lookahead = args.lookahead_gb * 1e9
+
+    def nbytes(o, v):
+        return 8.0 * (3 * (o + v) ** 3 + o * o * v * v + o * v + o + v)
+
+    def generator():
+        st = torch.cuda.Stream()
+        for r, (o, v, seed, _, _) in enumerate(reqs):
+            with cv:
+                cv.wait_for(lambda: pending_bytes[0] + nbytes(o, v) <= lookahead or pending_bytes[0] == 0)
+                pending_bytes[0] += nbytes(o, v)
+            t0 = time.perf_counter()
+            with torch.cuda.stream(st):
+                d = synth.make_amplitudes_device(o, v, seed, "cuda")
+            st.synchronize()
+            gen_s[0] += time.perf_counter() - t0
+            devs[r] = d
+            ready[r].set()
 
     def collector():
-        for n in range(len(reqs)):
-            while tickets[n] is None:
-                time.sleep(0.001)
-            st, res = tc.tc_wait(ctx, tickets[n], 24 * 3600 * 1000)
-            results[n] = (st, res.seconds, res.queue_seconds, res.e_t)
+        # poll every submitted request, so a finished small job releases its
+        # inputs while a large one still runs
+        nxt, outstanding, left = 0, [], n
+        while left:
+            while nxt < n and tickets[nxt] is not None:
+                outstanding.append(nxt)
+                nxt += 1
+            still = []
+            for r in outstanding:
+                st_, res = tc.tc_poll(ctx, tickets[r])
+                if st_ == tc.TC_ENOTREADY:
+                    still.append(r)
+                    continue
+                results[r] = (st_, res.seconds, res.queue_seconds, res.e_t)
+                devs[r] = None
+                left -= 1
+                with cv:
+                    pending_bytes[0] -= nbytes(reqs[r][0], reqs[r][1])
+                    cv.notify_all()
+            outstanding = still
+            time.sleep(0.005)
         done.set()
 
-    th = threading.Thread(target=collector)
-    th.start()
+    gth = threading.Thread(target=generator, daemon=True)
+    cth = threading.Thread(target=collector, daemon=True)
+    gth.start()
+    cth.start()
+    late = []
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
-        for n, (o, v, _, prec, s) in enumerate(reqs):
-            delay = arrivals[n] - (time.perf_counter() - t0)
+        for r, (o, v, _, prec, s) in enumerate(reqs):
+            delay = arrivals[r] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            d = devs[n]
-            tickets[n] = tc.tc_submit(ctx, o, v, d["eps"], d["t1"], d["t2"], d["ovvv"], d["ovoo"], d["ovov"],
-                                      prec=prec, slices=s, device_inputs=True)
+            ready[r].wait()
+            submit_t[r] = time.perf_counter() - t0
+            late.append(submit_t[r] - arrivals[r])
+            d = devs[r]
+            tickets[r] = tc.tc_submit(ctx, o, v, d["eps"], d["t1"], d["t2"], prec=prec, slices=s,
+                                      device_inputs=True, B=d["B"])
         done.wait()
         makespan = time.perf_counter() - t0
-    th.join()
     stats = tc.tc_serve_stats_get(ctx)
     tc.tc_finalize(ctx)
-    ok = [r for r in results if r[0] == tc.TC_OK]
-    lat = np.array([r[1] for r in ok])
-    que = np.array([r[2] for r in ok])
-    flops = sum(alg_flops(o, v) for (o, v, _, _, _) in reqs)
-    by = lambda p: np.array([r[1] for r, q in zip(results, reqs) if q[3] == p and r[0] == tc.TC_OK])
+    ok = [r for r in range(n) if results[r][0] == tc.TC_OK]
+    lat = np.array([late[r] + results[r][1] for r in ok])
+    que = np.array([results[r][2] for r in ok])
+
+    def pct(x):
+        return ({"n": int(len(x)), "p50_s": float(np.percentile(x, 50)), "p99_s": float(np.percentile(x, 99)),
+                 "mean_s": float(np.mean(x))} if len(x) else {"n": 0})
+
+    by_prec = {}
+    for name, p in (("fp64", 0), ("split", 1)):
+        by_prec[name] = pct(np.array([late[r] + results[r][1] for r in ok if reqs[r][3] == p]))
+    buckets = {}
+    for name, lo, hi in (("small <1e13 flop", 0, 1e13), ("medium 1e13-1e14", 1e13, 1e14), ("large >=1e14", 1e14, 1e99)):
+        buckets[name] = pct(np.array([late[r] + results[r][1] for r in ok if lo <= flops[r] < hi]))
     out = {
         "metric": "serving latency", "unit": "s", "higher_is_better": False, "n_gpus": 1,
         "value": float(np.percentile(lat, 99)), "p50_s": float(np.percentile(lat, 50)),
         "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
         "queue_p50_s": float(np.percentile(que, 50)), "queue_p99_s": float(np.percentile(que, 99)),
-        "jobs_per_s": len(ok) / makespan, "tflops_aggregate": flops / makespan / 1e12,
-        "rate_per_s": rate, "offered_load": rate / capacity, "requests": len(reqs), "completed": len(ok),
-        "fp64_requests": int(sum(1 for q in reqs if q[3] == 0)),
-        "p50_fp64_s": float(np.percentile(by(0), 50)) if len(by(0)) else None,
-        "p50_split_s": float(np.percentile(by(1), 50)) if len(by(1)) else None,
-        "makespan_s": makespan, "input_generation_s": t_gen,
+        "client_late_p99_s": float(np.percentile(late, 99)),
+        "jobs_per_s": len(ok) / makespan, "tflops_aggregate": sum(flops[r] for r in ok) / makespan / 1e12,
+        "rate_per_s": rate, "offered_load": rate / capacity, "capacity_model_jobs_per_s": capacity,
+        "requests": n, "completed": len(ok), "fp64_requests": int(sum(1 for q in reqs if q[3] == 0)),
+        "by_precision": by_prec, "by_size": buckets,
+        "makespan_s": makespan, "input_generation_s": gen_s[0],
         "iterations": stats.iterations, "graph_launches": stats.graph_launches,
         "mean_jobs_per_launch": stats.batched_jobs / max(1, stats.iterations),
-        "clocks": clk.summary(), "data": "synthetic (seeded request stream, inputs resident on the device)",
+        "hbm_budget_gb": budget / 1e9,
+        "clocks": clk.summary(),
+        "data": "synthetic (seeded request stream drawn on the device; DF factors, integrals assembled by the service)",
         "config": {"workload": "serving", "o": "U{6..32}", "v": "round(o*U[6,12])", "Q": "3(o+v)",
                    "fp64_share": args.fp64_share, "slices": args.slices, "prefix_of_stream": args.requests,
                    "arrivals": "Poisson (seeded)"},
@@ -366,6 +437,10 @@ def main():
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (0: --load x capacity)")
     ap.add_argument("--load", type=float, default=0.5, help="serving: offered load relative to estimated capacity")
     ap.add_argument("--fp64-share", type=float, default=0.5, help="serving: fraction of FP64 requests")
+    ap.add_argument("--budget-frac", type=float, default=0.55,
+                    help="serving: the library's HBM budget as a fraction of free device memory")
+    ap.add_argument("--lookahead-gb", type=float, default=40.0,
+                    help="serving: device memory for drawn but unfinished request inputs")
     args = ap.parse_args()
     if args.workload == "serving":
         return serving(args)
