@@ -16,6 +16,7 @@ def _tree(tmp_path, src):
     d = tmp_path / "paper_2512_01055_gb300" / "csrc"
     d.mkdir(parents=True)
     (d / "tc_split.cu").write_text(src)
+    (d / "tc_ptx.cuh").write_text("// shared helpers\n#pragma once\n")
     (tmp_path / "profiles").mkdir()
     return tmp_path
 
@@ -29,6 +30,9 @@ def test_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.kernel_source_hash("split") == h0
     p.write_text("int f(int x) {\n  return x + 2;\n}\n")
     assert bench.kernel_source_hash("split") != h0
+    p.write_text(base)
+    (tmp_path / "paper_2512_01055_gb300" / "csrc" / "tc_ptx.cuh").write_text("#pragma once\nint h();\n")
+    assert bench.kernel_source_hash("split") != h0          # the shared helpers count too
 
 
 def test_recorded_traffic_follows_the_hash(tmp_path, monkeypatch):
