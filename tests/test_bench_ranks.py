@@ -53,3 +53,18 @@ def test_reference_arm_other_ranks_exit_quietly():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_line_states_what_it_timed():
+    """The reference arm's JSON line on the tiny workload: one sampled triplet per step, projected."""
+    import json
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "tiny_o6_v36", "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["projected"] is True
+    assert line["step"] == "one sampled occupied triplet" and line["steps"] == 2
+    assert line["config"]["workload"] == "tiny_o6_v36" and line["dtype"] == "f64"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and 0 <= cb["cores"] <= cb["cores_available"] + 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
