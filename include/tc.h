@@ -111,7 +111,14 @@ typedef struct {
 tc_status tc_init(tc_ctx **ctx, const tc_options *opt);
 
 /* E_(T) from HOST arrays (Eqs. 1-5).  Blocking.  Copies the inputs to the
- * device, runs the hot path, returns E_(T) in out->e_t.
+ * device, runs the hot path, returns E_(T) in out->e_t.  On the split path
+ * t2, ovvv, ovoo and ovov are copied on a second stream in chunks of their
+ * first (occupied) index, and each chunk is sliced just before the first
+ * block of triplets that reads it, so from page-locked host arrays the copies
+ * overlap the tensor-core work (pageable arrays work too, without the
+ * overlap); prep_seconds then sums the slicing of all chunks, and
+ * kernel_seconds includes the later chunks' slicing and any wait for their
+ * copies.  No copy reads the caller's arrays after the call returns.
  * prec: tc_precision, or < 0 for the context default.  slices: 2..4 for
  * TC_SPLIT_BF16, <= 0 for the default; ignored for TC_FP64.
  * e_ijk (optional, may be NULL): host array [o][o][o] that receives the

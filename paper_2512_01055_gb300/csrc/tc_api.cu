@@ -61,11 +61,25 @@ double alg_flops(int o, int v) {
   return 2.0 * (O * O * O * V * V * V * V + O * O * O * O * V * V * V);
 }
 
+// Inputs that are still arriving (tc_energy, split path): chunk c holds the
+// rows of t2, ovvv, ovoo and ovov whose first occupied index lies in
+// [c ? p_end[c - 1] : 0, p_end[c]); ready[c] is recorded once they are on the
+// device.  Triplets run in the order i >= j >= k with i non-decreasing, and a
+// triplet reads only rows p <= i, so a block of triplets needs the chunks up
+// to the one holding its last triplet's i.
+struct Staging {
+  int nchunk = 0;
+  const int *p_end = nullptr;
+  const cudaEvent_t *ready = nullptr;
+};
+
 // The hot path on device-resident inputs.  Caller holds ctx->mu.
 // subset (optional): process these triplets only; e_sub receives their sums.
+// stg (optional, split path, no subset): slice each chunk of the inputs once
+// it has arrived, just before the first block of triplets that reads it.
 tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, int slices, double *e_ijk_dev,
                      cudaStream_t st, tc_result *out, const std::vector<int4> *subset = nullptr,
-                     std::vector<double> *e_sub = nullptr) {
+                     std::vector<double> *e_sub = nullptr, const Staging *stg = nullptr) {
   const bool split = (prec == TC_SPLIT_BF16);
   const int nt = split ? tc::split_tile() : tc::fp64_tile();
   const tc::Dims d = tc::plan::make_dims(o, v, nt, subset ? (int)subset->size() : -1,
@@ -91,7 +105,32 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
   if (e_ijk_dev) TC_CUDA(ctx, cudaMemsetAsync(e_ijk_dev, 0, sizeof(double) * (size_t)o * o * o, st));
   int launches = 1;                                      // reduce_jobs
   int nblocks = 0;                                       // split path: blocks of triplets
-  if (split) {
+  if (stg && (!split || subset)) return fail(ctx, TC_EINTERNAL, "staged inputs need the split path on all triplets");
+  int staged = 0;                                        // chunks sliced so far
+  const int npev = stg ? 2 * (stg->nchunk + 1) : 0;
+  while ((int)ctx->pev.size() < npev) {
+    cudaEvent_t e = nullptr;
+    TC_CUDA(ctx, cudaEventCreate(&e));
+    ctx->pev.push_back(e);
+  }
+  // wait for and slice every chunk that starts at or below first index imax
+  auto stage_upto = [&](int imax) -> tc_status {
+    for (; staged < stg->nchunk && (staged ? stg->p_end[staged - 1] : 0) <= imax; ++staged) {
+      const int p0 = staged ? stg->p_end[staged - 1] : 0, p1 = stg->p_end[staged];
+      TC_CUDA(ctx, cudaStreamWaitEvent(st, stg->ready[staged], 0));
+      TC_CUDA(ctx, cudaEventRecord(ctx->pev[2 + 2 * staged], st));
+      TC_CUDA(ctx, tc::launch_split_prep_range(SL, in, ctx->ws_split.p, st, p0, p1));
+      TC_CUDA(ctx, cudaEventRecord(ctx->pev[3 + 2 * staged], st));
+      launches += tc::split_prep_range_launches();
+    }
+    return TC_OK;
+  };
+  if (split && stg) {
+    TC_CUDA(ctx, cudaEventRecord(ctx->pev[0], st));
+    TC_CUDA(ctx, tc::launch_split_prep_common(SL, in, ctx->ws_split.p, st));
+    TC_CUDA(ctx, cudaEventRecord(ctx->pev[1], st));
+    launches += tc::split_prep_launches() - tc::split_prep_range_launches();
+  } else if (split) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
     TC_CUDA(ctx, tc::launch_split_prep(SL, in, ctx->ws_split.p, st));
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
@@ -113,6 +152,10 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
       static thread_local tc::EnBatch eb;
       for (int blk = 0; blk < nblocks; ++blk) {
         const int t0 = blk * nb, nt = std::min(nb, d.n_trip - t0);
+        if (stg) {
+          const tc_status ss = stage_upto(tab[(size_t)t0 + nt - 1].x);
+          if (ss != TC_OK) return ss;
+        }
         wb = tc::WtBatch{};
         wb.njobs = 1;
         wb.err = w.err;
@@ -138,6 +181,12 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     launches += 1;
+  }
+  if (stg) {
+    // the remaining chunks (read by no triplet, e.g. o = 1): the stream still
+    // waits for their copies before the read-back
+    const tc_status ss = stage_upto(o);
+    if (ss != TC_OK) return ss;
   }
   {
     tc::RedBatch rb{};
@@ -176,7 +225,15 @@ tc_status run_device(tc_ctx *ctx, int o, int v, const tc::Inputs &in, int prec, 
       out->wterm_seconds = wsum;
     }
   }
-  if (split) {
+  if (split && stg) {
+    double psum = 0.0;
+    for (int c = 0; c <= stg->nchunk; ++c) {
+      float ms = 0.f;
+      TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->pev[2 * c], ctx->pev[2 * c + 1]));
+      psum += 1e-3 * ms;
+    }
+    out->prep_seconds = psum;
+  } else if (split) {
     float ms = 0.f;
     TC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]));
     out->prep_seconds = 1e-3 * ms;
@@ -281,6 +338,7 @@ tc_status tc_init(tc_ctx **out, const tc_options *opt) {
   if (cudaSetDevice(ctx->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost((void **)&ctx->host_out, 4 * sizeof(double)) != cudaSuccess ||
       cudaEventCreate(&ctx->ev[0]) != cudaSuccess || cudaEventCreate(&ctx->ev[1]) != cudaSuccess ||
       cudaEventCreate(&ctx->ev[2]) != cudaSuccess || cudaEventCreate(&ctx->ev[3]) != cudaSuccess) {
@@ -311,6 +369,12 @@ void tc_finalize(tc_ctx *ctx) {
   if (ctx->host_out) cudaFreeHost(ctx->host_out);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
   for (auto &e : ctx->wev) if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->cev) if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->pev) if (e) cudaEventDestroy(e);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -530,15 +594,52 @@ tc_status tc_energy(tc_ctx *ctx, int o, int v, const double *eps, const double *
   TC_CUDA(ctx, ctx->in_ovov.ensure(sizeof(double) * n_ovov));
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_eps.p, eps, sizeof(double) * n_eps, cudaMemcpyHostToDevice, st));
   TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t1.p, t1, sizeof(double) * n_t1, cudaMemcpyHostToDevice, st));
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t2.p, t2, sizeof(double) * n_t2, cudaMemcpyHostToDevice, st));
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovvv.p, ints->ovvv, sizeof(double) * n_ovvv, cudaMemcpyHostToDevice, st));
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovoo.p, ints->ovoo, sizeof(double) * n_ovoo, cudaMemcpyHostToDevice, st));
-  TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovov.p, ints->ovov, sizeof(double) * n_ovov, cudaMemcpyHostToDevice, st));
   tc::Inputs in{(const double *)ctx->in_eps.p, (const double *)ctx->in_t1.p, (const double *)ctx->in_t2.p,
                 (const double *)ctx->in_ovvv.p, (const double *)ctx->in_ovoo.p, (const double *)ctx->in_ovov.p};
   double *e_ijk_dev = e_ijk ? (double *)ctx->in_eps.p + n_eps : nullptr;
   std::memset(out, 0, sizeof *out);
-  s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
+  if (prec == TC_SPLIT_BF16) {
+    // The four large inputs go over on the copy stream in chunks of occupied
+    // indices (their first index), and each chunk is sliced just before the
+    // first block of triplets that reads it, so the copies of the later
+    // chunks overlap the first blocks' tensor-core work.  At most 64 chunks.
+    const int per = std::max(1, (o + 63) / 64), nchunk = (o + per - 1) / per;
+    std::vector<int> p_end((size_t)nchunk);
+    for (int c = 0; c < nchunk; ++c) p_end[(size_t)c] = std::min(o, (c + 1) * per);
+    while ((int)ctx->cev.size() < nchunk) {
+      cudaEvent_t e = nullptr;
+      TC_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ctx->cev.push_back(e);
+    }
+    const struct { void *dst; const double *src; size_t row; } big[4] = {
+        {ctx->in_t2.p, t2, (size_t)o * v * v},
+        {ctx->in_ovvv.p, ints->ovvv, (size_t)v * v * v},
+        {ctx->in_ovoo.p, ints->ovoo, (size_t)v * o * o},
+        {ctx->in_ovov.p, ints->ovov, (size_t)v * o * v}};
+    cudaError_t ce = cudaSuccess;
+    for (int c = 0; c < nchunk && ce == cudaSuccess; ++c) {
+      const size_t p0 = c ? (size_t)p_end[(size_t)c - 1] : 0, np = (size_t)p_end[(size_t)c] - p0;
+      for (int k = 0; k < 4 && ce == cudaSuccess; ++k)
+        ce = cudaMemcpyAsync((double *)big[k].dst + p0 * big[k].row, big[k].src + p0 * big[k].row,
+                             sizeof(double) * np * big[k].row, cudaMemcpyHostToDevice, ctx->copy_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(ctx->cev[(size_t)c], ctx->copy_stream);
+    }
+    if (ce == cudaSuccess) {
+      const Staging stg{nchunk, p_end.data(), ctx->cev.data()};
+      s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out, nullptr, nullptr, &stg);
+    }
+    // no copy may still read the caller's arrays once this call returns
+    const cudaError_t ce2 = cudaStreamSynchronize(ctx->copy_stream);
+    if (ce == cudaSuccess) ce = ce2;
+    if (ce != cudaSuccess)
+      return fail(ctx, TC_ECUDA, "input copies failed: %s", cudaGetErrorString(ce));
+  } else {
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_t2.p, t2, sizeof(double) * n_t2, cudaMemcpyHostToDevice, st));
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovvv.p, ints->ovvv, sizeof(double) * n_ovvv, cudaMemcpyHostToDevice, st));
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovoo.p, ints->ovoo, sizeof(double) * n_ovoo, cudaMemcpyHostToDevice, st));
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->in_ovov.p, ints->ovov, sizeof(double) * n_ovov, cudaMemcpyHostToDevice, st));
+    s = run_device(ctx, o, v, in, prec, slices, e_ijk_dev, st, out);
+  }
   if (s != TC_OK) return s;
   if (e_ijk) {
     TC_CUDA(ctx, cudaMemcpyAsync(e_ijk, e_ijk_dev, sizeof(double) * (size_t)o * o * o, cudaMemcpyDeviceToHost, st));

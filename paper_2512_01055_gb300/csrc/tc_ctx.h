@@ -52,6 +52,9 @@ struct tc_ctx {
   double *host_out = nullptr;               // pinned read-back slot
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};     // kernel timing
   std::vector<cudaEvent_t> wev;             // split path: a pair around each W-term launch (grown on demand)
+  cudaStream_t copy_stream = nullptr;       // tc_energy: host-to-device copies of the inputs, by occupied-index chunk
+  std::vector<cudaEvent_t> cev;             // tc_energy: one per chunk, recorded on copy_stream after its copies
+  std::vector<cudaEvent_t> pev;             // staged split path: a pair around each chunk's slicing
   std::mutex serve_mu;                      // guards creation of the serving engine
   tc::Server *server = nullptr;
 };

@@ -146,8 +146,16 @@ int split_tile();
 int split_orb_per_item(int o, int v, int S);
 SplitGeom split_geom(int o, int v, int S);
 SplitLayout split_layout(int o, int v, int S);
+// Operand images and FP32 copies of a job: launch_split_prep builds all of
+// them; launch_split_prep_common builds those of t1 and the orbital energies
+// and launch_split_prep_range those read from t2, ovvv, ovoo and ovov rows
+// whose first occupied index lies in [p0, p1) (what a triplet (i, j, k) with
+// i >= j >= k reads lies in the rows p <= i).
 cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st);
+cudaError_t launch_split_prep_common(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st);
+cudaError_t launch_split_prep_range(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st, int p0, int p1);
 int split_prep_launches();
+int split_prep_range_launches();
 WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt);
 // Energy job of triplets [t0, t0 + nt); encodes its tensor map (driver entry point).
 cudaError_t en_job(EnJob *out, const Dims &d, const SplitLayout &L, const void *ws, const Inputs &in, const Work &w,

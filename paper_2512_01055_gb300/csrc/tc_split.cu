@@ -923,8 +923,12 @@ tc_energy_kernel(const __grid_constant__ EnBatch B) {
 //   kind 4  B  [r][q][nc][hv]    row z,      K f:  t_rq^zf                = t2[r][q][z][f]
 //   kind 5  B  [r][q][nc][ho]    row z,      K l:  -(r z | q l)           = -ovoo[r][z][q][l]
 // (kinds 2 and 3 read t_lp^.. as t_pl^.. with the virtual pair swapped, which
-// keeps the reads coalesced).
-__global__ void build_image(int kind, const double *__restrict__ src, SplitGeom G, unsigned char *__restrict__ out) {
+// keeps the reads coalesced).  Every kind's halves are ordered by the first
+// occupied index of the tensor they read (p, or r), so the threads of one
+// first-index range are the contiguous range [e_begin, e_end) of the image's
+// (half, row) index.
+__global__ void build_image(int kind, const double *__restrict__ src, SplitGeom G, long long e_begin,
+                            long long e_end, unsigned char *__restrict__ out) {
   const int o = G.o, v = G.v, S = G.S;
   const bool isA = kind < 4;
   const int rows = isA ? MROWS : G.nc;
@@ -932,9 +936,10 @@ __global__ void build_image(int kind, const double *__restrict__ src, SplitGeom 
   const int kmax = (kind == 0 || kind == 1 || kind == 4) ? v : o;
   const long long nhalf = isA ? (long long)o * G.mt * nh : (long long)o * o * G.nch * nh;
   const size_t half_bytes = (size_t)rows * 16;
-  const long long total = nhalf * rows;
+  const long long total = min(nhalf * rows, e_end);
   const long long vv = (long long)v * v;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+  for (long long e = e_begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % rows);
     const long long hb = e / rows;
     const int h = (int)(hb % nh);
@@ -1010,22 +1015,36 @@ __global__ void f32_hilo(const double *__restrict__ in, int n, float *__restrict
 }
 
 // FP32 (p u|q w) in both orders, rows vc floats long (zero beyond v):
-// out[0][p][u][q][w] = ovov[p][u][q][w], out[1][q][w][p][u] = ovov[p][u][q][w].
-__global__ void ovov_f32(const double *__restrict__ ovov, int o, int v, int vc, float *__restrict__ out) {
-  const long long half = (long long)o * v * o * vc, n = 2 * half;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int h = e >= half;
-    long long r = e - h * half;
+// out[0][p][u][q][w] = ovov[p][u][q][w], out[1][q][w][p][u] = ovov[p][u][q][w],
+// for the entries read from ovov rows p in [p0, p1) (ovov's first index: the
+// first index of out[0], the third of out[1]).
+__global__ void ovov_f32(const double *__restrict__ ovov, int o, int v, int vc, int p0, int p1,
+                         float *__restrict__ out) {
+  const int np = p1 - p0;
+  const long long half = (long long)o * v * o * vc, part = (long long)np * v * o * vc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * part;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int h = e >= part;
+    long long r = e - h * part;
     const int x3 = (int)(r % vc);
     r /= vc;
-    const int x2 = (int)(r % o);
-    r /= o;
-    const int x1 = (int)(r % v), x0 = (int)(r / v);
+    int x0, x1, x2;
+    if (h == 0) {
+      x2 = (int)(r % o);
+      r /= o;
+      x1 = (int)(r % v);
+      x0 = p0 + (int)(r / v);
+    } else {
+      x2 = p0 + (int)(r % np);
+      r /= np;
+      x1 = (int)(r % v);
+      x0 = (int)(r / v);
+    }
     float val = 0.f;
     if (x3 < v)
       val = (float)(h == 0 ? ovov[(((long long)x0 * v + x1) * o + x2) * v + x3]
                            : ovov[(((long long)x2 * v + x3) * o + x0) * v + x1]);
-    out[e] = val;
+    out[h * half + (((long long)x0 * v + x1) * o + x2) * vc + x3] = val;
   }
 }
 
@@ -1160,23 +1179,46 @@ SplitLayout split_layout(int o, int v, int S) {
   return L;
 }
 
-cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st) {
+namespace {
+// (half, row) entries of image `kind` per value of its first occupied index.
+long long image_per_first(int kind, const SplitGeom &g) {
+  const int nh = (kind == 0 || kind == 1 || kind == 4) ? g.hv : g.ho;
+  return kind < 4 ? (long long)g.mt * nh * MROWS : (long long)g.o * g.nch * nh * g.nc;
+}
+constexpr int PREP_BLOCKS = 152 * 16, PREP_THREADS = 256;
+}  // namespace
+
+cudaError_t launch_split_prep_common(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st) {
   const SplitGeom &g = L.g;
   unsigned char *b = (unsigned char *)ws;
-  const int blocks = 152 * 16, thr = 256;
-  build_image<<<blocks, thr, 0, st>>>(0, in.ovvv, g, b + L.pa);
-  build_image<<<blocks, thr, 0, st>>>(1, in.ovvv, g, b + L.pa2);
-  build_image<<<blocks, thr, 0, st>>>(2, in.t2, g, b + L.hc);
-  build_image<<<blocks, thr, 0, st>>>(3, in.t2, g, b + L.hc2);
-  build_image<<<blocks, thr, 0, st>>>(4, in.t2, g, b + L.tb);
-  build_image<<<blocks, thr, 0, st>>>(5, in.ovoo, g, b + L.hb);
-  f32_rows<<<blocks, thr, 0, st>>>(in.t1, g.o, g.v, g.vc, (float *)(b + L.t1f));
-  f32_hilo<<<blocks, thr, 0, st>>>(in.eps, g.o + g.v, (float *)(b + L.epsf));
-  ovov_f32<<<blocks, thr, 0, st>>>(in.ovov, g.o, g.v, g.vc, (float *)(b + L.ovovf));
+  f32_rows<<<PREP_BLOCKS, PREP_THREADS, 0, st>>>(in.t1, g.o, g.v, g.vc, (float *)(b + L.t1f));
+  f32_hilo<<<PREP_BLOCKS, PREP_THREADS, 0, st>>>(in.eps, g.o + g.v, (float *)(b + L.epsf));
   return cudaGetLastError();
 }
 
+cudaError_t launch_split_prep_range(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st, int p0,
+                                    int p1) {
+  const SplitGeom &g = L.g;
+  if (p0 < 0 || p1 > g.o || p0 >= p1) return cudaErrorInvalidValue;
+  unsigned char *b = (unsigned char *)ws;
+  const size_t off[6] = {L.pa, L.pa2, L.hc, L.hc2, L.tb, L.hb};
+  const double *src[6] = {in.ovvv, in.ovvv, in.t2, in.t2, in.t2, in.ovoo};
+  for (int kind = 0; kind < 6; ++kind) {
+    const long long per = image_per_first(kind, g);
+    build_image<<<PREP_BLOCKS, PREP_THREADS, 0, st>>>(kind, src[kind], g, per * p0, per * p1, b + off[kind]);
+  }
+  ovov_f32<<<PREP_BLOCKS, PREP_THREADS, 0, st>>>(in.ovov, g.o, g.v, g.vc, p0, p1, (float *)(b + L.ovovf));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_prep(const SplitLayout &L, const Inputs &in, void *ws, cudaStream_t st) {
+  cudaError_t e = launch_split_prep_common(L, in, ws, st);
+  if (e != cudaSuccess) return e;
+  return launch_split_prep_range(L, in, ws, st, 0, L.g.o);
+}
+
 int split_prep_launches() { return 9; }
+int split_prep_range_launches() { return 7; }
 
 WtJob wt_job(const SplitLayout &L, const void *ws, const int4 *trip, int t0, int nt) {
   const unsigned char *b = (const unsigned char *)ws;

@@ -88,6 +88,30 @@ def test_split_is_deterministic_and_host_entry_agrees():
     np.testing.assert_array_equal(e1, eh)
 
 
+@pytest.mark.parametrize("o,v,pinned", [(1, 9, False), (2, 7, False), (5, 21, True), (70, 12, False), (67, 10, True)])
+def test_host_entry_staged_copies_match_device_entry(o, v, pinned):
+    """tc_energy copies t2, ovvv, ovoo and ovov in chunks of occupied indices
+    (one index per chunk up to o = 64, two beyond) and slices each chunk just
+    before the first block of triplets that reads it: E_T and every triplet's
+    energy equal the device entry's bit for bit, from pageable and from pinned
+    host arrays, with no triplets (o = 1) and with chunks of two indices."""
+    import torch
+    job = synth.make_job(o, v, 31 + o)
+    rd, ed = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
+    keep = []
+    if pinned:
+        def pin(a):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            keep.append(t)
+            return t.numpy()
+        job = dataclasses.replace(job, eps=pin(job.eps), t1=pin(job.t1), t2=pin(job.t2), ovvv=pin(job.ovvv),
+                                  ovoo=pin(job.ovoo), ovov=pin(job.ovov))
+    rh, eh = gpu_util.energy_host(job, prec=SPLIT, slices=3, want_trip=True)
+    assert rh.e_t == rd.e_t
+    np.testing.assert_array_equal(eh, ed)
+    assert rh.launches >= rd.launches
+
+
 def test_split_matches_fp64_path_closely():
     job = synth.make_job(5, 40, 22)
     rf, ef = gpu_util.energy_dev(job, prec=tc.TC_FP64, want_trip=True)
