@@ -20,7 +20,7 @@
 // X(jik,bac) and the hole parts of X(kji,cba) and X(kij,cab); F(i,k,j) and
 // F(j,k,i) hold the other four pairs.  Each F is one GEMM with M = v^2 row
 // pairs (x, y), N = v and K = 2v + 2o (four segments), so the tensor cores run
-// with N up to 224 instead of the 16-wide panels a tile-local W would allow.
+// with N up to 256 instead of the 16-wide panels a tile-local W would allow.
 //
 // W-term kernel.  One launch forms one F for a block of triplets; a work item
 // is (128-row M tile, triplet, N chunk), M-tile-major so the triplets of the
@@ -76,13 +76,14 @@ constexpr int KB = 16;                    // K values per block (one MMA)
 constexpr int MROWS = 128;                // rows of an M tile
 constexpr int A_BLK = MROWS * KB * 2;     // bytes of one A slice block
 constexpr int A_HALF = MROWS * 16;        // bytes of one A slice half (8 K values)
-constexpr int NCMAX = 224;                // widest N chunk
+constexpr int NCMAX = 256;                // widest N chunk: two accumulators of 256 columns fill TMEM
+constexpr int NCMAX_S4 = 224;             // widest N chunk at s = 4, where more than DEFER stages must fit
+constexpr int NC_NARROW = 224;            // chunks up to this width: at most 7 column groups per drain thread
 constexpr int MAXS = 4;
 constexpr int MAX_STAGES = 8;
 constexpr int NPROD = 3;
 constexpr int THREADS = 384;
 constexpr int DRAIN_THREADS = 256;
-constexpr int MAXG = (NCMAX / 16 + 1) / 2;   // 16-column groups a drain thread holds
 constexpr int SMEM_DYN_MAX = 232448 - 2048;  // opt-in limit minus static shared memory and slack
 // Longest run of K blocks accumulated in one tensor-core accumulator (see above).
 constexpr int KCHAIN = 16;
@@ -191,7 +192,9 @@ __device__ __forceinline__ void wt_src(const WtJob &J, int m, int nci, int p, in
   b = J.hb + ((((size_t)r * G.o + p) * G.nch + nci) * G.ho + h) * bhb;
 }
 
-template <int S>
+// MG: 16-column groups a drain thread holds, 7 for chunks of up to 224
+// columns, 8 up to 256.
+template <int S, int MG>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_wterm_kernel(const __grid_constant__ WtBatch B) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -390,7 +393,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
       const int nchain = (nkb + KCHAIN - 1) / KCHAIN;
       const int ng = nc / 16, gsplit = (ng + 1) / 2;
       const int g0 = half ? gsplit : 0, my = half ? ng - gsplit : gsplit;
-      float v[MAXG][16];                              // this thread's row: running sum over chains
+      float v[MG][16];                                // this thread's row: running sum over chains
       for (int ch = 0; ch < nchain; ++ch) {
         if (et == 0) drain_ok = mbar_wait(&accfull_bar, aphase, &abort_flag, B.err, ERR_TIMEOUT_ACCFULL) ? 1 : 0;
         drain_bar();
@@ -403,12 +406,12 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
         const bool last = ch + 1 == nchain;
         if (ch == 0 && !last) {
 #pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2)
+          for (int gi2 = 0; gi2 < MG; ++gi2)
             if (gi2 < my) tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), v[gi2]);
           tmem_wait_ld();
-        } else {
+        } else if constexpr (MG <= 7) {
 #pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+          for (int gi2 = 0; gi2 < MG; ++gi2) {
             if (gi2 >= my) break;
             float l0[16], l1[16];
             tmem_ld16(trow + (uint32_t)((g0 + gi2) * 16), l0);
@@ -418,6 +421,25 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
             for (int e = 0; e < 16; ++e) {
               const float x = last ? l0[e] + l1[e] : l0[e];
               v[gi2][e] = ch > 0 ? x + v[gi2][e] : x;
+            }
+          }
+        } else {
+          // the same sums, eight columns at a time: with 8 groups of 16 in v,
+          // 16-column temporaries would spill
+#pragma unroll
+          for (int gi2 = 0; gi2 < MG; ++gi2) {
+            if (gi2 >= my) break;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              float l0[8], l1[8];
+              tmem_ld8(trow + (uint32_t)((g0 + gi2) * 16 + 8 * hh), l0);
+              if (last) tmem_ld8(trow + (uint32_t)(nc + (g0 + gi2) * 16 + 8 * hh), l1);
+              tmem_wait_ld();
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const float x = last ? l0[e] + l1[e] : l0[e];
+                v[gi2][8 * hh + e] = ch > 0 ? x + v[gi2][8 * hh + e] : x;
+              }
             }
           }
         }
@@ -450,7 +472,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
           const int q = lane & 3;                       // place in the quad
           const int r0 = row - q;                       // the quad's first row
 #pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+          for (int gi2 = 0; gi2 < MG; ++gi2) {
             if (gi2 >= my) break;                       // warp-uniform
             float4 X[4];
 #pragma unroll
@@ -484,7 +506,7 @@ tc_wterm_kernel(const __grid_constant__ WtBatch B) {
           const size_t st = (g == 1) ? (size_t)vc : (size_t)vo * vc;
           float *dst = Wf + ((g == 1) ? (size_t)p * vo * vc : (size_t)p * vc) + c + (size_t)zb * st;
 #pragma unroll
-          for (int gi2 = 0; gi2 < MAXG; ++gi2) {
+          for (int gi2 = 0; gi2 < MG; ++gi2) {
             if (gi2 >= my) break;
 #pragma unroll
             for (int e = 0; e < 16; ++e)
@@ -1069,26 +1091,38 @@ WtShape wt_shape(int S, int ncmax) {
   return s;
 }
 
-template <int S>
-void wt_params(const WtBatch &b, int grid, size_t smem, void **args, cudaKernelNodeParams *p) {
+using WtKernel = void (*)(WtBatch);
+
+// The W-term kernel instance for S slices and a widest N chunk of ncmax columns.
+WtKernel wt_kernel(int S, int ncmax) {
+  const bool wide = ncmax > NC_NARROW;
+  switch (S) {
+    case 2: return wide ? tc_wterm_kernel<2, 8> : tc_wterm_kernel<2, 7>;
+    case 3: return wide ? tc_wterm_kernel<3, 8> : tc_wterm_kernel<3, 7>;
+    default: return tc_wterm_kernel<4, 7>;
+  }
+}
+
+void wt_params(WtKernel fn, const WtBatch &b, int grid, size_t smem, void **args, cudaKernelNodeParams *p) {
   args[0] = (void *)&b;
   *p = cudaKernelNodeParams{};
-  p->func = (void *)tc_wterm_kernel<S>;
+  p->func = (void *)fn;
   p->gridDim = dim3(grid);
   p->blockDim = dim3(THREADS);
   p->sharedMemBytes = (unsigned)smem;
   p->kernelParams = args;
 }
 
-// Item offsets, shared-memory plan and grids of a W-term batch and an energy
-// batch; sets the kernels' shared-memory limits.
-cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, int *egrid, size_t *wsmem) {
+// Item offsets, shared-memory plan, grids and W-term kernel instance of a
+// W-term batch and an energy batch; sets the kernels' shared-memory limits.
+cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, int *egrid, size_t *wsmem,
+                    WtKernel *wfn) {
   if (S < 2 || S > MAXS || wb.njobs < 1 || wb.njobs > MAX_BATCH || eb.njobs != wb.njobs) return cudaErrorInvalidValue;
   long long total = 0;
   int ncmax = 16;
   for (int j = 0; j < wb.njobs; ++j) {
     WtJob &J = wb.job[j];
-    if (J.g.nc > NCMAX || J.g.S != S) return cudaErrorInvalidValue;
+    if (J.g.nc > (S >= 4 ? NCMAX_S4 : NCMAX) || J.g.S != S) return cudaErrorInvalidValue;
     J.item0 = total;
     total += (long long)J.g.mt * J.nt * J.g.nch;
     ncmax = std::max(ncmax, J.g.nc);
@@ -1108,12 +1142,8 @@ cudaError_t prepare(WtBatch &wb, EnBatch &eb, int S, int num_sms, int *wgrid, in
   eb.total_items = etotal;
   *wgrid = (int)std::max<long long>(1, std::min<long long>(num_sms, total));
   *egrid = (int)std::max<long long>(1, std::min<long long>(num_sms, etotal));
-  cudaError_t e = cudaSuccess;
-  switch (S) {
-    case 2: e = cudaFuncSetAttribute(tc_wterm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
-    case 3: e = cudaFuncSetAttribute(tc_wterm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
-    default: e = cudaFuncSetAttribute(tc_wterm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem); break;
-  }
+  *wfn = wt_kernel(S, ncmax);
+  cudaError_t e = cudaFuncSetAttribute(*wfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(tc_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, EN_SMEM);
   return e;
 }
@@ -1141,7 +1171,8 @@ SplitGeom split_geom(int o, int v, int S) {
   g.hv = (v + 7) / 8;
   g.ho = (o + 7) / 8;
   const int vp = g.kbv * KB;
-  g.nch = (vp + NCMAX - 1) / NCMAX;
+  const int ncmax = S >= 4 ? NCMAX_S4 : NCMAX;
+  g.nch = (vp + ncmax - 1) / ncmax;
   g.nc = ((vp + g.nch - 1) / g.nch + 15) / 16 * 16;
   g.vc = (v + 3) / 4 * 4;
   // Triplets per block: about 64 W-term items per SM of a 152-SM GPU in each
@@ -1310,16 +1341,13 @@ cudaError_t split_block_params(WtBatch *wb, EnBatch &eb, int S, int num_sms, voi
                                cudaKernelNodeParams *wp, cudaKernelNodeParams *ep) {
   int wgrid = 1, egrid = 1;
   size_t wsmem = 0;
-  cudaError_t e = prepare(wb[0], eb, S, num_sms, &wgrid, &egrid, &wsmem);
+  WtKernel wfn = nullptr;
+  cudaError_t e = prepare(wb[0], eb, S, num_sms, &wgrid, &egrid, &wsmem, &wfn);
   if (e != cudaSuccess) return e;
   for (int f = 0; f < SPLIT_WT_LAUNCHES; ++f) {
     if (f > 0) wb[f] = wb[0];
     for (int j = 0; j < wb[f].njobs; ++j) wb[f].job[j].gsel = f;
-    switch (S) {
-      case 2: wt_params<2>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
-      case 3: wt_params<3>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
-      default: wt_params<4>(wb[f], wgrid, wsmem, &wargs[f], &wp[f]); break;
-    }
+    wt_params(wfn, wb[f], wgrid, wsmem, &wargs[f], &wp[f]);
   }
   eargs[0] = (void *)&eb;
   *ep = cudaKernelNodeParams{};
@@ -1335,7 +1363,8 @@ cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cud
                                cudaEvent_t w0, cudaEvent_t w1) {
   int wgrid = 1, egrid = 1;
   size_t wsmem = 0;
-  cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem);
+  WtKernel wfn = nullptr;
+  cudaError_t e = prepare(wb, eb, S, num_sms, &wgrid, &egrid, &wsmem, &wfn);
   if (e != cudaSuccess) return e;
   if (w0 && (e = cudaEventRecord(w0, st)) != cudaSuccess) return e;
   // Programmatic launches: each kernel of the chain may start its CTAs on SMs
@@ -1354,11 +1383,7 @@ cudaError_t launch_split_block(WtBatch &wb, EnBatch &eb, int S, int num_sms, cud
   // F(i,j,k), F(i,k,j), F(j,k,i) in this order (the batch is copied at each launch)
   for (int f = 0; f < SPLIT_WT_LAUNCHES; ++f) {
     for (int j = 0; j < wb.njobs; ++j) wb.job[j].gsel = f;
-    switch (S) {
-      case 2: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<2>, wb); break;
-      case 3: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<3>, wb); break;
-      default: e = cudaLaunchKernelEx(&cfg, tc_wterm_kernel<4>, wb); break;
-    }
+    e = cudaLaunchKernelEx(&cfg, wfn, wb);
     if (e != cudaSuccess) return e;
   }
   if (w1 && (e = cudaEventRecord(w1, st)) != cudaSuccess) return e;

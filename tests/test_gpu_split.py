@@ -112,6 +112,29 @@ def test_host_entry_staged_copies_match_device_entry(o, v, pinned):
     assert rh.launches >= rd.launches
 
 
+@pytest.mark.parametrize("o,v", [(2, 250), (2, 230)])
+def test_wide_n_chunk_against_oracle(o, v):
+    """v = 250 and 230 give one N chunk of 256 and 240 columns: the widest
+    accumulators (all 512 TMEM columns at 256) and eight 16-column groups per
+    drain thread, at s = 2 and 3; s = 4 keeps chunks of at most 224."""
+    job = synth.make_job(o, v, 50 + v)
+    ref = oracle.energy_by_triplets(job)
+    for s in (2, 3, 4):
+        r, _ = gpu_util.energy_dev(job, prec=SPLIT, slices=s)
+        print(f"o={o} v={v} s={s} |dE|/|E|={abs(r.e_t - ref) / abs(ref):.3e}")
+        assert abs(r.e_t - ref) <= rel_bound(s, ref, o, v)
+
+
+def test_two_wide_n_chunks_match_fp64_path():
+    """v = 460: two N chunks of 240 (three of 160 before chunks could reach 256)."""
+    job = synth.make_job(3, 460, 61)
+    rf, ef = gpu_util.energy_dev(job, prec=tc.TC_FP64, want_trip=True)
+    rs, es = gpu_util.energy_dev(job, prec=SPLIT, slices=3, want_trip=True)
+    assert abs(rs.e_t - rf.e_t) <= 1e-6 * abs(rf.e_t)
+    scale = np.abs(ef).max()
+    assert np.abs(es - ef).max() <= 1e-5 * scale
+
+
 def test_split_matches_fp64_path_closely():
     job = synth.make_job(5, 40, 22)
     rf, ef = gpu_util.energy_dev(job, prec=tc.TC_FP64, want_trip=True)
