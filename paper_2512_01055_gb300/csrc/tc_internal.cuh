@@ -90,7 +90,7 @@ struct SplitGeom {
   int mt;                // M tiles: ceil(v^2 / 128)
   int kbv, kbo;          // 16-wide blocks over a virtual / an occupied index (kbv sets the N padding)
   int hv, ho;            // 8-wide K halves over a virtual / an occupied index
-  int nch, nc;           // N chunks and their width (multiple of 16, <= 224)
+  int nch, nc;           // N chunks and their width (multiple of 16, <= 256; <= 224 at s = 4)
   int vc;                // innermost extent of the W buffer and FP32 copies (v rounded up to 4)
   int nb;                // triplets per block (capacity of the W buffer)
 };
