@@ -66,6 +66,28 @@ def test_results_alone_equal_results_in_the_mix():
         assert abs(ref[n] - e) <= (1e-9 if p == tc.TC_FP64 else 1e-6) * abs(e)
 
 
+def test_wide_and_narrow_n_chunks_in_one_batch():
+    """A batch runs on one W-term kernel instance: the one with eight drain
+    groups as soon as one of its jobs has an N chunk wider than 224 columns
+    (v = 240, 250), which then also serves the narrow jobs; each result is the
+    same bits as alone."""
+    spec = [(3, 240, 121, 3), (6, 40, 122, 3), (8, 50, 123, 3), (4, 250, 124, 2), (5, 33, 125, 2)]
+    jobs = [(synth.make_job(o, v, seed), SPLIT, s) for (o, v, seed, s) in spec]
+    ref = [alone(j, p, s) for (j, p, s) in jobs]
+    ctx = tc.tc_init(0, max_inflight=8, iteration_ms=5)
+    try:
+        tickets = submit_all(ctx, jobs)
+        for n, t in enumerate(tickets):
+            st, res = tc.tc_wait(ctx, t, 120000)
+            assert st == tc.TC_OK, (n, tc.status_str(st))
+            assert res.e_t == ref[n], (n, res.e_t, ref[n])
+        stats = tc.tc_serve_stats_get(ctx)
+        assert stats.completed == len(jobs) and stats.failed == 0
+        assert stats.batched_jobs > stats.iterations
+    finally:
+        tc.tc_finalize(ctx)
+
+
 def test_device_resident_inputs():
     jobs = [(synth.make_job(o, v, seed), prec, s) for (o, v, seed, prec, s) in MIX[:6]]
     devs = [gpu_util.to_device(j) for (j, _, _) in jobs]
